@@ -1,0 +1,73 @@
+"""Test-only helpers: brute-force minimum cuts and refinement invariants.
+
+Nothing here is part of the CUDA path or of the oracle; these are the
+independent checks the oracle is pinned against.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+
+
+def brute_min_cut(n: int, eu, ev, w=None):
+    """Minimum over all 2^(n-1)-1 bipartitions (vertex 0 fixed on side A).
+    Returns (value, list of minimising side masks as int bitmasks of B)."""
+    eu = np.asarray(eu, np.int64)
+    ev = np.asarray(ev, np.int64)
+    w = np.ones(len(eu), np.int64) if w is None else np.asarray(w, np.int64)
+    masks = np.arange(1, 1 << (n - 1), dtype=np.int64) << 1  # bit v set => v in B; bit 0 never set
+    bu = (masks[:, None] >> eu[None, :]) & 1
+    bv = (masks[:, None] >> ev[None, :]) & 1
+    cut = ((bu != bv) * w[None, :]).sum(axis=1)
+    best = int(cut.min())
+    return best, [int(x) for x in masks[cut == best]]
+
+
+def cut_value(eu, ev, side, w=None):
+    eu = np.asarray(eu)
+    ev = np.asarray(ev)
+    side = np.asarray(side, bool)
+    w = np.ones(len(eu), np.int64) if w is None else np.asarray(w, np.int64)
+    return int(((side[eu] != side[ev]) * w).sum())
+
+
+def induced_edges(off, adj, verts):
+    """Edge list (local ids, u < v) of G[verts] for an ascending vertex array."""
+    verts = np.asarray(verts, np.int64)
+    pos = {int(v): i for i, v in enumerate(verts)}
+    eu, ev = [], []
+    for i, v in enumerate(verts):
+        for u in adj[off[v]:off[v + 1]]:
+            j = pos.get(int(u))
+            if j is not None and i < j:
+                eu.append(i); ev.append(j)
+    return np.array(eu, np.int32), np.array(ev, np.int32)
+
+
+def is_connected(n, eu, ev) -> bool:
+    if n <= 1:
+        return True
+    A = sp.coo_matrix((np.ones(len(eu)), (eu, ev)), shape=(n, n))
+    return connected_components(A, directed=False)[0] == 1
+
+
+def clusters_of(labels):
+    """dict label -> ascending vertex array (labels >= 0 only)."""
+    labels = np.asarray(labels)
+    idx = np.nonzero(labels >= 0)[0]
+    order = idx[np.argsort(labels[idx], kind="stable")]
+    lab = labels[order]
+    if len(order) == 0:
+        return {}
+    cuts = np.nonzero(np.diff(lab))[0] + 1
+    return {int(lab[a]): order[a:b] for a, b in zip(np.r_[0, cuts], np.r_[cuts, len(order)])}
+
+
+def min_labels(labels):
+    """Replace each output id by the smallest vertex id of its cluster."""
+    labels = np.asarray(labels)
+    out = np.full(len(labels), -1, np.int64)
+    for _, vs in clusters_of(labels).items():
+        out[vs] = vs.min()
+    return out
