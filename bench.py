@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the WCC refinement hot path on one GB300 per rank.
+
+One step = the whole path over one synthetic input: device CSR build from the
+edge list (wcc_create_graph_from_edges) + the refinement (wcc_run: grouping by
+input label, refinement kernel, output numbering).  Inputs (edge list and input
+clustering) are resident in HBM when the timed region starts; L2 is flushed
+(a 512 MiB device write) before every timed step, outside the step's events.
+
+Workload: the LFR-style benchmark graph with 100,000 vertices (power-law
+degrees, exponent 2.5, mean 20, max 1,000; power-law community sizes 20-2,000,
+exponent 1.5; mixing 0.3; 10% of communities merged pairwise through 1-2
+bridges), seed = rank, criterion floor(log10 n), min size 2 (s_pre = s_post =
+1 as in the paper's experiments).
+
+Multi-GPU (torchrun): input clusters are independent (Algorithms 1-2 iterate
+over them with no exchange), so each rank refines its own instance with no
+data-path collective: weak scaling.
+
+``--impl reference`` times the CPU oracle (the plain C refinement used as the
+parity reference) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "WCC clusters/s and edges/s at 1 GB300 (batched/served vs plain), %HBM roofline; p50/p99"
+WORKLOAD = "lfr_100k"
+MIN_SIZE = 2
+
+
+def workload(rank: int):
+    import synth
+    return synth.lfr_like(100_000, seed=rank, min_size=MIN_SIZE)
+
+
+def describe(w) -> dict:
+    return {"workload": f"{WORKLOAD}: LFR-style graph, {w.n} vertices, {w.m} undirected edges, "
+                        f"{w.n_clusters} input clusters (10% merged pairwise by 1-2 bridges), "
+                        "criterion floor(log10 n), min size 2",
+            "n": w.n, "m": w.m, "input_clusters": w.n_clusters, "min_size": MIN_SIZE,
+            "rule": "log10", "l2": "flushed before every timed step (512 MiB device write)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
+                 "--format=csv,noheader,nounits", "-i", str(gpu_index), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout=5.0):
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t_begin: float, t_end: float):
+        if not self.proc:
+            return None
+        rows = [l for (t, l) in self.lines if t_begin <= t <= t_end]
+        if not rows:
+            rows = [l for (_, l) in self.lines[-3:]]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            parts = [p.strip() for p in r.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_step(w):
+    import oracle
+    off, adj = oracle.build_csr(w.n, w.src, w.dst)
+    out, st = oracle.wcc(w.n, off, adj, w.labels, w.min_size)
+    return out
+
+
+def cpu_baseline(w, budget_s: float = 12.0):
+    """The oracle as it stands, single-threaded, repeated on the full workload
+    until ~budget_s of CPU time: edges/s."""
+    import oracle
+    oracle.build()
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle_step(w)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > budget_s or len(times) >= 50:
+            break
+    mean = sum(times) / len(times)
+    return {"value": w.m / mean, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"the full {WORKLOAD} workload (CSR build + refinement), "
+                      f"{len(times)} repetitions, mean {mean * 1e3:.1f} ms each",
+            "clusters_per_s": w.n_clusters / mean}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = workload(0)
+    for _ in range(args.warmup):
+        oracle_step(w)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(w)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = w.m * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": describe(w),
+            "clusters_per_s": w.n_clusters * args.steps / total,
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the full {WORKLOAD} workload per step"},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2509_02590_gb300 as wcc
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = workload(rank)
+    dev = torch.device("cuda", local)
+    src_d = torch.from_numpy(w.src).to(dev)
+    dst_d = torch.from_numpy(w.dst).to(dev)
+    lab_d = torch.from_numpy(w.labels).to(dev)
+    out_d = torch.empty_like(lab_d)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(mode="batched"):
+        g = wcc.WccGraph.from_edges(src_d, dst_d, w.n)
+        try:
+            _, st = g.run(lab_d, min_size=w.min_size, mode=mode, out=out_d, stats=True)
+        finally:
+            g.close()
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    # correctness guard on rank 0 (outside the timed region)
+    barrier()
+
+    sampler = ClockSampler(local)
+    sampler.wait_first()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    refine_ms, refine_bytes = [], []
+    barrier()
+    l0 = wcc.wcc_kernel_launches()
+    t_begin = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        st = step()
+        ev[k][1].record(stream)
+        refine_ms.append(st["ms_refine"])
+        refine_bytes.append(st["alg_bytes"])
+    barrier()
+    t_end = time.perf_counter()
+    launches = wcc.wcc_kernel_launches() - l0
+    sampler.stop()
+    clocks = sampler.summary(t_begin, t_end)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        mw = torch.tensor([w.m, w.n_clusters], dtype=torch.float64, device=dev)
+        dist.all_reduce(mw)
+        m_all, k_all = float(mw[0].item()), float(mw[1].item())
+    else:
+        m_all, k_all = float(w.m), float(w.n_clusters)
+    value = m_all * args.steps / (total_ms / 1e3)
+    clusters_per_s = k_all * args.steps / (total_ms / 1e3)
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+
+    # plain path (one kernel launch per work item), same workload
+    plain = None
+    if args.plain_steps > 0:
+        pms = []
+        for k in range(args.plain_steps):
+            flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step("plain")
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms.append(a.elapsed_time(b))
+        pm = sum(pms) / len(pms)
+        plain = {"edges_per_s": w.m / (pm / 1e3), "clusters_per_s": w.n_clusters / (pm / 1e3),
+                 "ms_per_step": pm, "steps": len(pms)}
+
+    # end to end through the public API with pinned host buffers
+    src_h = torch.from_numpy(w.src).pin_memory()
+    dst_h = torch.from_numpy(w.dst).pin_memory()
+    lab_h = torch.from_numpy(w.labels).pin_memory()
+    out_h = torch.empty_like(lab_h).pin_memory()
+    e2e_t = []
+    for k in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 1):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with wcc.WccGraph.from_edges(src_h, dst_h, w.n) as g:
+            g.run(lab_h, min_size=w.min_size, out=out_h)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_t = e2e_t[2:] or e2e_t
+    e2e_mean = sum(e2e_t) / len(e2e_t)
+    e2e_local = torch.tensor([e2e_mean], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
+    e2e_value = m_all / float(e2e_local.item())
+    # the result must match the device-buffer run
+    ok = bool(np.array_equal(out_h.numpy(), out_d.cpu().numpy()))
+
+    # roofline of the dominant kernel (the refinement kernel)
+    peak, peak_kind = hbm_peak()
+    r_ms = sum(refine_ms) / len(refine_ms)
+    r_bytes = sum(refine_bytes) / len(refine_bytes)
+    achieved = r_bytes / (r_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_refine", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_kind, "alg_bytes_per_launch": r_bytes,
+                "ms_per_launch": r_ms, "share_of_step": r_ms / (total_ms / args.steps)}
+    prof = os.path.join(ROOT, "profiles", "k_refine_lfr_100k.traffic.json")
+    if os.path.exists(prof):
+        try:
+            roofline["traffic"] = json.load(open(prof)).get("traffic_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": describe(w) | {"mode": "batched", "parallelism": f"independent x{world}"},
+                "clusters_per_s": clusters_per_s, "p50_ms": p50, "p99_ms": p99,
+                "plain": plain,
+                "batched_over_plain": (value / (plain["edges_per_s"] * world)) if plain else None,
+                "e2e": {"value": e2e_value, "unit": "edges/s",
+                        "h2d_bytes_per_step": int(8 * w.m + 4 * w.n),
+                        "d2h_bytes_per_step": int(4 * w.n), "ms_per_step": 1e3 * e2e_mean,
+                        "matches_device_run": ok},
+                "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,158 @@
+/*
+ * wcc.h -- C ABI of the GB300 Well-Connected Clusters (WCC) refinement library.
+ *
+ * WCC (paper Section 2.3, Algorithms 2 and 3, with the connected component
+ * refinement CCR of Section 2.2, Algorithm 1) takes a graph G and a
+ * clustering C and returns the clusters of C refined until each one is well
+ * connected: every input cluster is split into connected components, low
+ * degree vertices are peeled, an exact minimum edge cut is computed, and a
+ * cluster whose cut is at or below the criterion f(n) (Section 2; log10 n in
+ * Section 3) is bisected on that cut and both sides are refined again, until
+ * every part is accepted or is smaller than the size threshold.
+ *
+ * Every step runs in this library's CUDA kernels on one GPU.  There is no CPU
+ * fallback: without a usable GPU every call returns WCC_ERR_CUDA.
+ *
+ * Conventions for every function:
+ *   - Status codes are returned; nothing throws across the ABI.  On any
+ *     status other than WCC_OK / WCC_PENDING, wcc_last_error() returns a
+ *     thread-local message describing the failure, and output buffers are
+ *     left unspecified.
+ *   - The caller owns every input and output buffer and keeps it valid for
+ *     the duration of the call.  Handles returned by the library are owned by
+ *     the caller until the matching destroy call.
+ *   - on_device = 1: pointer arguments marked "host or device" are CUDA
+ *     device pointers (e.g. torch.Tensor.data_ptr() of a CUDA tensor) and
+ *     `stream` (a cudaStream_t, NULL = the legacy default stream) orders the
+ *     library's work after the caller's prior work on that stream.
+ *     on_device = 0: they are host pointers; the library copies them.
+ *   - All calls are synchronous with respect to the host unless stated.
+ *   - Vertex ids are int32 in [0, n); edge offsets are int64.
+ */
+#ifndef WCC_H
+#define WCC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wcc_graph wcc_graph;
+typedef struct wcc_server wcc_server;
+
+typedef enum {
+  WCC_OK = 0,
+  WCC_PENDING = 1,        /* request not finished yet (wcc_poll) */
+  WCC_ERR_INVALID = -1,   /* malformed argument or graph */
+  WCC_ERR_OOM = -2,       /* device memory (or a configured budget) exhausted */
+  WCC_ERR_CUDA = -3,      /* CUDA runtime / launch failure, or no GPU */
+  WCC_ERR_TIMEOUT = -4,   /* a bounded device-side wait ran out */
+  WCC_ERR_BUSY = -5,      /* request can never fit the server's budget */
+  WCC_ERR_INTERNAL = -6   /* a consistency check inside the library failed */
+} wcc_status;
+
+/* Criterion f(n) of Section 2 in exact integer form: a cluster of n vertices
+ * whose minimum cut is c fails iff c <= T(n), where T(n) is
+ *   LOG10:  largest t with 10^t <= n   (floor(log10 n); the rule of Section 3)
+ *   LOG2:   largest t with 2^t <= n
+ *   SQRT:   largest t with t*t <= n
+ *   LINEAR: floor(num * n / den)       (f(n) = k n with k = num/den) */
+typedef enum {
+  WCC_RULE_LOG10 = 0,
+  WCC_RULE_LOG2 = 1,
+  WCC_RULE_SQRT = 2,
+  WCC_RULE_LINEAR = 3
+} wcc_rule_kind;
+
+typedef struct {
+  int32_t kind;  /* wcc_rule_kind */
+  int32_t reserved;
+  int64_t num;   /* LINEAR only: 0 <= num < 2^31 */
+  int64_t den;   /* LINEAR only: 0 < den < 2^31 */
+} wcc_threshold_rule;
+
+/* Execution schedule of wcc_run.  Both give bit-identical results.
+ *   BATCHED: one persistent cooperative kernel drains a device-side work
+ *            queue holding every work item (input clusters and the parts
+ *            produced by splits), many items in flight at once.
+ *   PLAIN:   one kernel launch per work item, driven by a host loop. */
+typedef enum { WCC_MODE_BATCHED = 0, WCC_MODE_PLAIN = 1 } wcc_mode;
+
+typedef struct {
+  int64_t in_clusters;   /* distinct input labels >= 0 */
+  int64_t out_clusters;  /* accepted clusters */
+  int64_t items;         /* work items processed */
+  int64_t splits;        /* items bisected on their min cut */
+  int64_t peeled;        /* vertices removed by peeling */
+  int64_t ni_passes;     /* contraction passes (maximum-adjacency orderings) */
+  int64_t sw_phases;     /* Stoer-Wagner phases */
+  int64_t max_item;      /* largest input cluster refined (vertices) */
+  int64_t alg_bytes;     /* algorithmic HBM bytes of the run */
+  double ms_membership;  /* device time: grouping vertices by input label */
+  double ms_refine;      /* device time: the refinement kernel(s) */
+  double ms_output;      /* device time: numbering the accepted clusters */
+  double ms_total;       /* host wall time of the call */
+} wcc_stats;
+
+/* Create a graph from a CSR.  row_off[n+1] (int64, row_off[0] = 0,
+ * non-decreasing, row_off[n] = nnz) and cols[nnz] (int32) describe a simple
+ * undirected graph: each row strictly ascending (no repeated neighbours), no
+ * self-loop, and v in row u iff u in row v.  The whole CSR is checked on the
+ * device; a violation returns WCC_ERR_INVALID.  The graph keeps its own
+ * device copy; the input buffers (host or device) may be freed on return.
+ * Graph data structure: the CSR part of the double-index format of
+ * Section 2.1. */
+int wcc_create_graph(const int64_t *row_off, const int32_t *cols, int64_t n, int64_t nnz,
+                     int on_device, void *stream, wcc_graph **out);
+
+/* Create a graph from an edge list src[m], dst[m] (host or device, int32 ids
+ * in [0, n)), built on the device: both directions, self-loops and repeated
+ * edges dropped, rows sorted.  An id outside [0, n) returns
+ * WCC_ERR_INVALID. */
+int wcc_create_graph_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                int on_device, void *stream, wcc_graph **out);
+
+/* Number of vertices / directed CSR entries (2 x undirected edges). */
+int64_t wcc_graph_num_vertices(const wcc_graph *g);
+int64_t wcc_graph_nnz(const wcc_graph *g);
+
+/* Copy the graph's CSR out (host or device buffers of n+1 and nnz
+ * entries). */
+int wcc_graph_export_csr(const wcc_graph *g, int64_t *row_off, int32_t *cols, int on_device,
+                         void *stream);
+
+/* Refine a clustering (Algorithm 2 with CCR first).
+ *   clustering_in[n]  (host or device) int32: input cluster of each vertex,
+ *                     any value >= 0; -1 = vertex in no cluster.
+ *   rule              criterion (NULL = LOG10).
+ *   min_size          smallest part kept: the paper's s_pre = s_post = s is
+ *                     min_size = s + 1 (Section 3 uses s = 1, min_size 2);
+ *                     values below 2 act as 2.
+ *   mode              wcc_mode.
+ *   clustering_out[n] (host or device) int32: accepted clusters numbered
+ *                     0..K-1 in ascending order of their smallest vertex id,
+ *                     -1 for every vertex in no accepted cluster.  Written
+ *                     only on WCC_OK.  May not alias clustering_in.
+ *   stats             optional (NULL to skip).
+ * Returns WCC_OK, WCC_ERR_INVALID (bad rule or sizes), WCC_ERR_OOM,
+ * WCC_ERR_CUDA, WCC_ERR_TIMEOUT (a device-side queue wait exceeded its
+ * limit) or WCC_ERR_INTERNAL. */
+int wcc_run(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+            int32_t min_size, int32_t mode, int32_t *clustering_out, int on_device, void *stream,
+            wcc_stats *stats);
+
+/* Release a graph (NULL is ignored). */
+void wcc_destroy_graph(wcc_graph *g);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (instrumentation: lets a caller count the kernels of a timed region). */
+int64_t wcc_kernel_launches(void);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *wcc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WCC_H */

@@ -1,0 +1,132 @@
+"""GB300 Well-Connected Clusters refinement (WCC, arXiv 2509.02590).
+
+The refinement runs in the CUDA library ``libwcc_gb300.so`` behind the C ABI
+of ``include/wcc.h``.  ``_binding`` exposes that ABI under the same names;
+:class:`WccGraph` below only marshals numpy arrays (host buffers) or CUDA
+torch tensors (device buffers, ordered on torch's current stream) into it.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding
+from ._binding import (WCC_MODE_BATCHED, WCC_MODE_PLAIN, WCC_RULE_LINEAR,  # noqa: F401
+                       WCC_RULE_LOG2, WCC_RULE_LOG10, WCC_RULE_SQRT, WccError, wcc_create_graph,
+                       wcc_create_graph_from_edges, wcc_destroy_graph, wcc_graph_export_csr,
+                       wcc_graph_nnz, wcc_graph_num_vertices, wcc_kernel_launches,
+                       wcc_last_error, wcc_run,
+                       wcc_stats, wcc_threshold_rule)
+
+_RULES = {"log10": WCC_RULE_LOG10, "log2": WCC_RULE_LOG2, "sqrt": WCC_RULE_SQRT,
+          "linear": WCC_RULE_LINEAR}
+_MODES = {"batched": WCC_MODE_BATCHED, "plain": WCC_MODE_PLAIN}
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _buf(x, dtype):
+    """(pointer, on_device, stream, keepalive) for a numpy array or torch tensor."""
+    if _is_torch(x):
+        import torch
+        tdt = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {tdt} tensor")
+        if x.is_cuda:
+            return x.data_ptr(), 1, torch.cuda.current_stream(x.device).cuda_stream, x
+        return x.data_ptr(), 0, 0, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, 0, 0, a
+
+
+def rule_struct(rule="log10", num: int = 1, den: int = 1) -> wcc_threshold_rule:
+    kind = _RULES[rule] if isinstance(rule, str) else int(rule)
+    return wcc_threshold_rule(kind, 0, num, den)
+
+
+class WccGraph:
+    """A graph resident on the GPU (owns a ``wcc_graph`` handle)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @classmethod
+    def from_csr(cls, row_off, cols, n: int | None = None) -> "WccGraph":
+        po, dev_o, st, ko = _buf(row_off, np.int64)
+        pc, dev_c, _, kc = _buf(cols, np.int32)
+        if dev_o != dev_c:
+            raise TypeError("row_off and cols must both be host or both be device buffers")
+        n = (len(ko) - 1) if n is None else n
+        return cls(wcc_create_graph(po, pc, n, len(kc), dev_o, st))
+
+    @classmethod
+    def from_edges(cls, src, dst, n: int) -> "WccGraph":
+        ps, dev_s, st, ks = _buf(src, np.int32)
+        pd, dev_d, _, kd = _buf(dst, np.int32)
+        if dev_s != dev_d or len(ks) != len(kd):
+            raise TypeError("src and dst must match in length and placement")
+        return cls(wcc_create_graph_from_edges(ps, pd, len(ks), n, dev_s, st))
+
+    @property
+    def n(self) -> int:
+        return wcc_graph_num_vertices(self.handle)
+
+    @property
+    def nnz(self) -> int:
+        return wcc_graph_nnz(self.handle)
+
+    def csr(self):
+        off = np.empty(self.n + 1, np.int64)
+        adj = np.empty(max(self.nnz, 1), np.int32)
+        wcc_graph_export_csr(self.handle, off.ctypes.data, adj.ctypes.data, 0, 0)
+        return off, adj[:self.nnz]
+
+    def run(self, labels, min_size: int = 2, rule="log10", num: int = 1, den: int = 1,
+            mode="batched", out=None, stats: bool = False):
+        """Refine ``labels`` (numpy -> numpy on the host path, CUDA tensor ->
+        CUDA tensor on the device path).  Returns ``out`` (and a stats dict
+        when ``stats``)."""
+        pin, dev, stream, kin = _buf(labels, np.int32)
+        if out is None:
+            if _is_torch(labels):
+                import torch
+                out = torch.empty_like(labels)
+            else:
+                out = np.empty(len(kin), np.int32)
+        pout, dev_o, _, kout = _buf(out, np.int32)
+        if dev_o != dev:
+            raise TypeError("labels and out must both be host or both be device buffers")
+        st = wcc_stats() if stats else None
+        r = rule_struct(rule, num, den)
+        m = _MODES[mode] if isinstance(mode, str) else int(mode)
+        wcc_run(self.handle, pin, r, min_size, m, pout, dev, stream, st)
+        if out is not kout and not _is_torch(out):
+            out[...] = kout
+        return (out, st.as_dict()) if stats else out
+
+    def close(self):
+        if self.handle:
+            wcc_destroy_graph(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["WccGraph", "WccError", "rule_struct", "wcc_create_graph",
+           "wcc_create_graph_from_edges", "wcc_run", "wcc_destroy_graph", "wcc_last_error",
+           "wcc_graph_num_vertices", "wcc_graph_nnz", "wcc_kernel_launches", "wcc_graph_export_csr", "wcc_stats",
+           "wcc_threshold_rule", "WCC_MODE_BATCHED", "WCC_MODE_PLAIN"]
+_ = ctypes

@@ -1,0 +1,136 @@
+"""ctypes binding of the C ABI in ``include/wcc.h`` (argument marshalling only).
+
+Every function here forwards to ``libwcc_gb300.so``; no step of the
+refinement runs in Python.  If the library is missing or cannot be loaded,
+importing this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwcc_gb300.so")
+
+WCC_OK = 0
+WCC_PENDING = 1
+WCC_ERR_INVALID = -1
+WCC_ERR_OOM = -2
+WCC_ERR_CUDA = -3
+WCC_ERR_TIMEOUT = -4
+WCC_ERR_BUSY = -5
+WCC_ERR_INTERNAL = -6
+
+WCC_RULE_LOG10, WCC_RULE_LOG2, WCC_RULE_SQRT, WCC_RULE_LINEAR = 0, 1, 2, 3
+WCC_MODE_BATCHED, WCC_MODE_PLAIN = 0, 1
+
+STATUS_NAMES = {0: "WCC_OK", 1: "WCC_PENDING", -1: "WCC_ERR_INVALID", -2: "WCC_ERR_OOM",
+                -3: "WCC_ERR_CUDA", -4: "WCC_ERR_TIMEOUT", -5: "WCC_ERR_BUSY",
+                -6: "WCC_ERR_INTERNAL"}
+
+
+class wcc_threshold_rule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("num", ctypes.c_int64), ("den", ctypes.c_int64)]
+
+
+class wcc_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "in_clusters", "out_clusters", "items", "splits", "peeled", "ni_passes", "sw_phases",
+        "max_item", "alg_bytes")] + [(f, ctypes.c_double) for f in (
+            "ms_membership", "ms_refine", "ms_output", "ms_total")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class WccError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (nvcc, sm_103a). "
+            "There is no CPU fallback.")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+    gpp = ctypes.POINTER(ctypes.c_void_p)
+    L.wcc_create_graph.argtypes = [vp, vp, i64, i64, c_int, vp, gpp]
+    L.wcc_create_graph.restype = c_int
+    L.wcc_create_graph_from_edges.argtypes = [vp, vp, i64, i64, c_int, vp, gpp]
+    L.wcc_create_graph_from_edges.restype = c_int
+    L.wcc_graph_num_vertices.argtypes = [vp]
+    L.wcc_graph_num_vertices.restype = i64
+    L.wcc_graph_nnz.argtypes = [vp]
+    L.wcc_graph_nnz.restype = i64
+    L.wcc_graph_export_csr.argtypes = [vp, vp, vp, c_int, vp]
+    L.wcc_graph_export_csr.restype = c_int
+    L.wcc_run.argtypes = [vp, vp, ctypes.POINTER(wcc_threshold_rule), i32, i32, vp, c_int, vp,
+                          ctypes.POINTER(wcc_stats)]
+    L.wcc_run.restype = c_int
+    L.wcc_destroy_graph.argtypes = [vp]
+    L.wcc_destroy_graph.restype = None
+    L.wcc_kernel_launches.argtypes = []
+    L.wcc_kernel_launches.restype = i64
+    L.wcc_last_error.argtypes = []
+    L.wcc_last_error.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def wcc_kernel_launches() -> int:
+    return int(lib.wcc_kernel_launches())
+
+
+def wcc_last_error() -> str:
+    return lib.wcc_last_error().decode(errors="replace")
+
+
+def _check(status: int) -> int:
+    if status not in (WCC_OK, WCC_PENDING):
+        raise WccError(status, wcc_last_error())
+    return status
+
+
+def wcc_create_graph(row_off: int, cols: int, n: int, nnz: int, on_device: int,
+                     stream: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.wcc_create_graph(row_off, cols, n, nnz, on_device, stream, ctypes.byref(out)))
+    return out.value
+
+
+def wcc_create_graph_from_edges(src: int, dst: int, m: int, n: int, on_device: int,
+                                stream: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.wcc_create_graph_from_edges(src, dst, m, n, on_device, stream, ctypes.byref(out)))
+    return out.value
+
+
+def wcc_graph_num_vertices(g: int) -> int:
+    return int(lib.wcc_graph_num_vertices(g))
+
+
+def wcc_graph_nnz(g: int) -> int:
+    return int(lib.wcc_graph_nnz(g))
+
+
+def wcc_graph_export_csr(g: int, row_off: int, cols: int, on_device: int, stream: int) -> None:
+    _check(lib.wcc_graph_export_csr(g, row_off, cols, on_device, stream))
+
+
+def wcc_run(g: int, clustering_in: int, rule: wcc_threshold_rule | None, min_size: int,
+            mode: int, clustering_out: int, on_device: int, stream: int,
+            stats: wcc_stats | None = None) -> None:
+    _check(lib.wcc_run(g, clustering_in, ctypes.byref(rule) if rule is not None else None,
+                       min_size, mode, clustering_out, on_device, stream,
+                       ctypes.byref(stats) if stats is not None else None))
+
+
+def wcc_destroy_graph(g: int) -> None:
+    lib.wcc_destroy_graph(g)

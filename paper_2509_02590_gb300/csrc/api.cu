@@ -1,0 +1,713 @@
+// api.cu -- the C ABI (include/wcc.h): graph handles, the refinement run
+// (membership grouping, queue seeding, the refinement kernel, output
+// numbering) and error reporting.
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+
+#include "internal.h"
+
+namespace wccg {
+
+static thread_local std::string g_last_error;
+
+void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+DevBuf::~DevBuf() { release(); }
+
+void DevBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+void *DevBuf::ensure(size_t b) {
+  if (b <= bytes && p) return p;
+  release();
+  size_t want = b < 256 ? 256 : b;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    (void)cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? WCC_ERR_OOM : WCC_ERR_CUDA,
+         "device allocation of " + std::to_string(want) + " bytes failed: " +
+             cudaGetErrorString(e));
+  }
+  bytes = want;
+  return p;
+}
+
+namespace {
+
+constexpr int TB = 256;
+
+inline unsigned blocks_for(int64_t n, int per = TB) {
+  int64_t b = (n + per - 1) / per;
+  if (b < 1) b = 1;
+  if (b > 0x7fffffff) b = 0x7fffffff;
+  return (unsigned)b;
+}
+
+int bitlen_u64(uint64_t x) {
+  int b = 0;
+  while (x) { ++b; x >>= 1; }
+  return b;
+}
+
+// ---------------------------------------------------------------- CSR checks
+// Warp per vertex: offsets in range and non-decreasing, ids in [0, n), no
+// self-loop, rows strictly ascending, and symmetry (v found in row u by
+// binary search).
+__global__ void k_validate_csr(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                               int64_t n, int64_t nnz, unsigned *err) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int64_t v = w;
+  const int64_t b = off[v], e = off[v + 1];
+  if (b < 0 || e < b || e > nnz) {
+    if (lane == 0) atomicOr(err, DERR_INVALID);
+    return;
+  }
+  for (int64_t q = b + lane; q < e; q += 32) {
+    int32_t u = adj[q];
+    bool bad = u < 0 || u >= n || u == v || (q > b && adj[q - 1] >= u);
+    if (!bad) {
+      int64_t lo = off[u], hi = off[u + 1];
+      if (lo < 0 || hi < lo || hi > nnz) {
+        bad = true;
+      } else {
+        while (lo < hi) {
+          int64_t mid = (lo + hi) >> 1;
+          if (adj[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        bad = !(lo < off[u + 1] && adj[lo] == v);
+      }
+    }
+    if (bad) atomicOr(err, DERR_INVALID);
+  }
+}
+
+// ---------------------------------------------------------------- CSR build
+__global__ void k_edge_keys(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                            int64_t m, int64_t n, int b, uint64_t *keys, unsigned *err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int32_t u = src[i], v = dst[i];
+  if (u < 0 || u >= n || v < 0 || v >= n) {
+    atomicOr(err, DERR_INVALID);
+    keys[2 * i] = keys[2 * i + 1] = ~0ull;
+    return;
+  }
+  if (u == v) {
+    keys[2 * i] = keys[2 * i + 1] = ~0ull;
+    return;
+  }
+  keys[2 * i] = ((uint64_t)u << b) | (uint64_t)v;
+  keys[2 * i + 1] = ((uint64_t)v << b) | (uint64_t)u;
+}
+
+// keep[i] = 1 for the first copy of each valid key (sorted input)
+__global__ void k_unique_flags(const uint64_t *__restrict__ keys, int64_t n2, uint32_t *keep,
+                               uint64_t invalid) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  uint64_t k = keys[i];
+  keep[i] = (k != invalid && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
+}
+
+__global__ void k_compact_edges(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ keep,
+                                const uint32_t *__restrict__ pos, int64_t n2, int b,
+                                int32_t *cols, int64_t *deg) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n2 || !keep[i]) return;
+  uint64_t k = keys[i];
+  int64_t u = (int64_t)(k >> b);
+  cols[pos[i]] = (int32_t)(k & ((1ull << b) - 1));
+  atomicAdd((unsigned long long *)&deg[u], 1ull);
+}
+
+// ---------------------------------------------------------------- membership
+__global__ void k_make_keys(const int32_t *__restrict__ lab, int64_t n, uint32_t *keys,
+                            uint32_t *vals, unsigned *maxkey, unsigned *err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned k = 0;
+  if (i < n) {
+    int32_t c = lab[i];
+    if (c < -1) atomicOr(err, DERR_INVALID);
+    k = c < 0 ? 0u : (unsigned)c + 1u;
+    keys[i] = k;
+    vals[i] = (uint32_t)i;
+  }
+  k = warp_max(k);
+  if ((threadIdx.x & 31) == 0 && k) atomicMax(maxkey, k);
+}
+
+__global__ void k_heads(const uint32_t *__restrict__ sk, int64_t n, uint32_t *head) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  head[i] = (sk[i] != 0 && (i == 0 || sk[i - 1] != sk[i])) ? 1u : 0u;
+}
+
+__global__ void k_starts(const uint32_t *__restrict__ head, const uint32_t *__restrict__ hidx,
+                         int64_t n, int64_t *cstart) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && head[i]) cstart[hidx[i]] = i;
+}
+
+__global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
+
+// degree of each vertex in sorted order (for the per-cluster degree sums)
+__global__ void k_sorted_deg(const uint32_t *__restrict__ sv, const int64_t *__restrict__ off,
+                             int64_t n, int64_t *dg) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t v = sv[i];
+  dg[i] = off[v + 1] - off[v];
+}
+
+struct SeedInfo {
+  unsigned long long max_n;     // largest kept cluster
+  unsigned long long max_dsum;  // largest degree sum of a kept cluster
+  unsigned err;                 // DERR_* bits
+  unsigned maxkey;              // largest label + 1
+  unsigned kept;                // clusters with >= min_size members
+  unsigned pad;
+};
+
+__global__ void k_keep(const int64_t *__restrict__ cstart, int64_t K, int min_size,
+                       uint32_t *keep, const int64_t *__restrict__ pdeg, SeedInfo *info) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long sz = 0, ds = 0;
+  if (c < K) {
+    sz = (unsigned long long)(cstart[c + 1] - cstart[c]);
+    bool k = (int64_t)sz >= min_size;
+    keep[c] = k ? 1u : 0u;
+    if (k) ds = (unsigned long long)(pdeg[cstart[c + 1]] - pdeg[cstart[c]]);
+    else sz = 0;
+  }
+  sz = warp_max(sz);
+  ds = warp_max(ds);
+  if ((threadIdx.x & 31) == 0) {
+    if (sz) atomicMax(&info->max_n, sz);
+    if (ds) atomicMax(&info->max_dsum, ds);
+  }
+}
+
+__global__ void k_seed(const int64_t *__restrict__ cstart, const uint32_t *__restrict__ keep,
+                       const uint32_t *__restrict__ qidx, int64_t K, int64_t skip, QSlot *ring,
+                       uint64_t cap) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= K || !keep[c]) return;
+  uint64_t q = qidx[c];
+  QSlot *s = &ring[q % cap];
+  s->item.vbeg = cstart[c] - skip;
+  s->item.n = (int32_t)(cstart[c + 1] - cstart[c]);
+  s->item.flags = ITEM_TOP;
+  s->seq = q;
+}
+
+// pool[i - skip] = sorted vertex; slot[v] = (queue index << 32) | rank
+__global__ void k_pool_slots(const uint32_t *__restrict__ sk, const uint32_t *__restrict__ sv,
+                             const uint32_t *__restrict__ head, const uint32_t *__restrict__ hidx,
+                             const int64_t *__restrict__ cstart,
+                             const uint32_t *__restrict__ keep, const uint32_t *__restrict__ qidx,
+                             int64_t n, int64_t skip, int32_t *pool,
+                             unsigned long long *slot) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || i < skip) return;
+  uint32_t v = sv[i];
+  pool[i - skip] = (int32_t)v;
+  int64_t c = (int64_t)hidx[i] + head[i] - 1;  // inclusive head count - 1
+  if (keep[c]) slot[v] = ((unsigned long long)qidx[c] << 32) | (unsigned)(i - cstart[c]);
+  (void)sk;
+}
+
+// ---------------------------------------------------------------- output
+__global__ void k_out_flags(const int32_t *__restrict__ lmin, int64_t n, uint32_t *flag) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = lmin[i] == (int32_t)i ? 1u : 0u;
+}
+
+__global__ void k_out_final(const int32_t *__restrict__ lmin, const uint32_t *__restrict__ rank,
+                            int64_t n, int32_t *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t r = lmin[i];
+  out[i] = r >= 0 ? (int32_t)rank[r] : -1;
+}
+
+// ---------------------------------------------------------------- helpers
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) WCC_CUDA(cudaSetDevice(dev));
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int current_device() {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    (void)cudaGetLastError();
+    fail(WCC_ERR_CUDA, std::string("no usable CUDA device: ") +
+                           (e != cudaSuccess ? cudaGetErrorString(e) : "device count is 0"));
+  }
+  int dev = 0;
+  WCC_CUDA(cudaGetDevice(&dev));
+  return dev;
+}
+
+void check_derr(unsigned err, const char *what) {
+  if (!err) return;
+  if (err & DERR_INVALID) fail(WCC_ERR_INVALID, std::string(what) + ": malformed input");
+  if (err & DERR_TIMEOUT)
+    fail(WCC_ERR_TIMEOUT, std::string(what) + ": a device-side queue wait exceeded its limit");
+  if (err & DERR_CAPACITY)
+    fail(WCC_ERR_INTERNAL, std::string(what) + ": an internal capacity bound was exceeded");
+  fail(WCC_ERR_INTERNAL, std::string(what) + ": internal consistency check failed");
+}
+
+// Limit of every device-side queue wait (WCC_WAIT_LIMIT_MS, default 30 s):
+// a CTA that waits longer sets DERR_TIMEOUT and leaves, so a fault in the
+// queue protocol ends the kernel instead of hanging the GPU.
+uint64_t wait_limit_ns() {
+  const char *e = getenv("WCC_WAIT_LIMIT_MS");
+  long long ms = e ? atoll(e) : 30000;
+  if (ms < 1) ms = 1;
+  return (uint64_t)ms * 1000000ull;
+}
+
+template <typename T>
+T read_back(const T *dev, cudaStream_t s) {
+  T h;
+  WCC_CUDA(cudaMemcpyAsync(&h, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+
+enum Ws {
+  W_KEYS, W_VALS, W_KEYS2, W_VALS2, W_TEMP, W_HEAD, W_HIDX, W_CSTART, W_PDEG, W_KEEP, W_QIDX,
+  W_POOL, W_SLOT, W_LMIN, W_RING, W_CTR, W_SLAB, W_INFO, W_OUT, W_IN, W_FLAG, W_RANK, W_DG,
+  W_COUNT
+};
+static_assert(W_COUNT <= 24, "workspace slots");
+
+struct Timer {
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool on;
+  explicit Timer(bool enable) : on(enable) {
+    if (on)
+      for (auto &e : ev) WCC_CUDA(cudaEventCreate(&e));
+  }
+  ~Timer() {
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  void mark(int i, cudaStream_t s) {
+    if (on) WCC_CUDA(cudaEventRecord(ev[i], s));
+  }
+  double ms(int a, int b) {
+    if (!on) return 0;
+    float f = 0;
+    WCC_CUDA(cudaEventElapsedTime(&f, ev[a], ev[b]));
+    return f;
+  }
+};
+
+void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, int32_t min_size,
+              int32_t mode, int32_t *lab_out, int on_device, cudaStream_t s, wcc_stats *stats) {
+  auto t_start = std::chrono::steady_clock::now();
+  const int64_t n = g->n;
+  wcc_threshold_rule r = rule ? *rule : wcc_threshold_rule{WCC_RULE_LOG10, 0, 0, 1};
+  if (r.kind < WCC_RULE_LOG10 || r.kind > WCC_RULE_LINEAR)
+    fail(WCC_ERR_INVALID, "unknown threshold rule kind " + std::to_string(r.kind));
+  if (r.kind == WCC_RULE_LINEAR &&
+      (r.den <= 0 || r.num < 0 || r.den >= (1ll << 31) || r.num >= (1ll << 31)))
+    fail(WCC_ERR_INVALID, "LINEAR rule needs 0 <= num < 2^31 and 0 < den < 2^31");
+  if (mode != WCC_MODE_BATCHED && mode != WCC_MODE_PLAIN)
+    fail(WCC_ERR_INVALID, "unknown mode " + std::to_string(mode));
+  if (min_size < 2) min_size = 2;
+  if (lab_in == nullptr || lab_out == nullptr)
+    fail(WCC_ERR_INVALID, "clustering_in and clustering_out must not be NULL");
+  if (lab_in == lab_out) fail(WCC_ERR_INVALID, "clustering_out may not alias clustering_in");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n == 0) {
+    if (stats) stats->ms_total = 0;
+    return;
+  }
+  Timer tm(stats != nullptr);
+  DevBuf *ws = g->ws;
+
+  // input labels on the device
+  const int32_t *d_in = lab_in;
+  if (!on_device) {
+    int32_t *p = static_cast<int32_t *>(ws[W_IN].ensure(4 * n));
+    WCC_CUDA(cudaMemcpyAsync(p, lab_in, 4 * n, cudaMemcpyHostToDevice, s));
+    d_in = p;
+  }
+  tm.mark(0, s);
+
+  // ---- a2: group vertices by input label (stable radix sort on label+1)
+  uint32_t *keys = static_cast<uint32_t *>(ws[W_KEYS].ensure(4 * n));
+  uint32_t *vals = static_cast<uint32_t *>(ws[W_VALS].ensure(4 * n));
+  uint32_t *keys2 = static_cast<uint32_t *>(ws[W_KEYS2].ensure(4 * n));
+  uint32_t *vals2 = static_cast<uint32_t *>(ws[W_VALS2].ensure(4 * n));
+  size_t temp_b = std::max(radix_temp_bytes(n), scan_temp_bytes(n + 1));
+  void *temp = ws[W_TEMP].ensure(temp_b);
+  SeedInfo *info = static_cast<SeedInfo *>(ws[W_INFO].ensure(sizeof(SeedInfo)));
+  WCC_CUDA(cudaMemsetAsync(info, 0, sizeof(SeedInfo), s));
+  k_make_keys<<<blocks_for(n), TB, 0, s>>>(d_in, n, keys, vals, &info->maxkey, &info->err); note_launch();
+  WCC_CUDA(cudaGetLastError());
+  SeedInfo h0 = read_back(info, s);
+  if (h0.err) check_derr(h0.err, "clustering_in");
+  const int bits = bitlen_u64(h0.maxkey);
+  uint32_t *sk = keys, *sv = vals;
+  if (radix_sort_pairs_u32(keys, vals, keys2, vals2, n, bits, temp, s)) {
+    sk = keys2;
+    sv = vals2;
+  }
+  uint32_t *head = static_cast<uint32_t *>(ws[W_HEAD].ensure(4 * (n + 1)));
+  uint32_t *hidx = static_cast<uint32_t *>(ws[W_HIDX].ensure(4 * (n + 1)));
+  k_heads<<<blocks_for(n), TB, 0, s>>>(sk, n, head); note_launch();
+  WCC_CUDA(cudaGetLastError());
+  // hidx[n] receives the number of distinct labels
+  exclusive_scan_u32(head, hidx, n, hidx + n, temp, s);
+  const int64_t K = (int64_t)read_back(hidx + n, s);
+  // unclustered vertices (key 0) sort first
+  int64_t skip = 0;
+  int64_t *cstart = static_cast<int64_t *>(ws[W_CSTART].ensure(8 * (K + 1)));
+  if (K > 0) {
+    k_starts<<<blocks_for(n), TB, 0, s>>>(head, hidx, n, cstart); note_launch();
+    k_set_i64<<<1, 1, 0, s>>>(cstart + K, n); note_launch();
+    WCC_CUDA(cudaGetLastError());
+    skip = read_back(cstart, s);
+  } else {
+    skip = n;
+  }
+
+  // per-cluster degree sums (prefix sums of degrees in sorted order)
+  int64_t *dg = static_cast<int64_t *>(ws[W_DG].ensure(8 * (n + 1)));
+  int64_t *pdeg = static_cast<int64_t *>(ws[W_PDEG].ensure(8 * (n + 1)));
+  uint32_t *keep = static_cast<uint32_t *>(ws[W_KEEP].ensure(4 * (K + 1)));
+  uint32_t *qidx = static_cast<uint32_t *>(ws[W_QIDX].ensure(4 * (K + 1)));
+  int64_t nkept = 0;
+  SeedInfo hi{};
+  if (K > 0) {
+    k_sorted_deg<<<blocks_for(n), TB, 0, s>>>(sv, g->off.as<int64_t>(), n, dg); note_launch();
+    WCC_CUDA(cudaMemsetAsync(dg + n, 0, 8, s));
+    exclusive_scan_i64(dg, pdeg, n + 1, nullptr, temp, s);
+    k_keep<<<blocks_for(K), TB, 0, s>>>(cstart, K, min_size, keep, pdeg, info); note_launch();
+    exclusive_scan_u32(keep, qidx, K, &info->kept, temp, s);
+    WCC_CUDA(cudaGetLastError());
+    hi = read_back(info, s);
+    nkept = (int64_t)hi.kept;
+  }
+
+  // ---- queue, pool, slots
+  const int dev = g->device;
+  const int max_ctas = refine_max_ctas(dev);
+  const int grid = max_ctas;
+  const uint64_t cap = (uint64_t)n + 2ull * grid + 1024;
+  int32_t *pool = static_cast<int32_t *>(ws[W_POOL].ensure(4 * std::max<int64_t>(n - skip, 1)));
+  auto *slot = static_cast<unsigned long long *>(ws[W_SLOT].ensure(8 * n));
+  auto *lmin = static_cast<int32_t *>(ws[W_LMIN].ensure(4 * n));
+  auto *ring = static_cast<QSlot *>(ws[W_RING].ensure(sizeof(QSlot) * cap));
+  auto *ctr = static_cast<RunCounters *>(ws[W_CTR].ensure(sizeof(RunCounters)));
+  WCC_CUDA(cudaMemsetAsync(slot, 0xff, 8 * n, s));
+  WCC_CUDA(cudaMemsetAsync(lmin, 0xff, 4 * n, s));
+  WCC_CUDA(cudaMemsetAsync(ctr, 0, sizeof(RunCounters), s));
+  if (nkept > 0) {
+    WCC_CUDA(cudaMemsetAsync(ring, 0xff, sizeof(QSlot) * cap, s));
+    k_seed<<<blocks_for(K), TB, 0, s>>>(cstart, keep, qidx, K, skip, ring, cap); note_launch();
+    k_pool_slots<<<blocks_for(n), TB, 0, s>>>(sk, sv, head, hidx, cstart, keep, qidx, n, skip,
+                                              pool, slot); note_launch();
+    WCC_CUDA(cudaGetLastError());
+    RunCounters c0{};
+    c0.tail = (unsigned long long)nkept;
+    c0.pending = nkept;
+    WCC_CUDA(cudaMemcpyAsync(ctr, &c0, sizeof(c0), cudaMemcpyHostToDevice, s));
+  }
+  tm.mark(1, s);
+
+  // ---- refinement
+  if (nkept > 0) {
+    size_t need = item_workspace_bytes((int64_t)hi.max_n, (int64_t)hi.max_dsum);
+    size_t slab_bytes = need > refine_smem_bytes() ? ((need + 255) & ~(size_t)255) : 256;
+    RefineParams p{};
+    p.off = g->off.as<int64_t>();
+    p.adj = g->adj.as<int32_t>();
+    p.n_vertices = n;
+    p.pool = pool;
+    p.slot = slot;
+    p.label_min = lmin;
+    p.ring = ring;
+    p.ring_cap = cap;
+    p.ctr = ctr;
+    p.rule_kind = r.kind;
+    p.rule_num = r.num;
+    p.rule_den = r.den;
+    p.min_size = min_size;
+    p.wait_limit_ns = wait_limit_ns();
+    p.smem_bytes = refine_smem_bytes();
+    p.slab_bytes = slab_bytes;
+    if (mode == WCC_MODE_BATCHED) {
+      p.slab = static_cast<char *>(ws[W_SLAB].ensure(slab_bytes * (size_t)grid));
+      p.single_item = 0;
+      launch_refine(p, grid, true, s);
+    } else {
+      p.slab = static_cast<char *>(ws[W_SLAB].ensure(slab_bytes));
+      p.single_item = 1;
+      unsigned long long tail = (unsigned long long)nkept;
+      for (unsigned long long j = 0; j < tail; ++j) {
+        p.single_index = j;
+        launch_refine(p, 1, false, s);
+        if (j + 1 == tail) {
+          RunCounters c = read_back(ctr, s);
+          if (c.error) break;
+          tail = c.tail;
+        }
+      }
+    }
+  }
+  tm.mark(2, s);
+  RunCounters hc{};
+  if (nkept > 0) {
+    hc = read_back(ctr, s);
+    check_derr(hc.error, "refinement");
+  }
+
+  // ---- a9: ids = rank of each accepted cluster's smallest vertex
+  uint32_t *flag = static_cast<uint32_t *>(ws[W_FLAG].ensure(4 * n));
+  uint32_t *rank = static_cast<uint32_t *>(ws[W_RANK].ensure(4 * n));
+  int32_t *d_out = lab_out;
+  if (!on_device) d_out = static_cast<int32_t *>(ws[W_OUT].ensure(4 * n));
+  k_out_flags<<<blocks_for(n), TB, 0, s>>>(lmin, n, flag); note_launch();
+  exclusive_scan_u32(flag, rank, n, nullptr, temp, s);
+  k_out_final<<<blocks_for(n), TB, 0, s>>>(lmin, rank, n, d_out); note_launch();
+  WCC_CUDA(cudaGetLastError());
+  tm.mark(3, s);
+  if (!on_device) WCC_CUDA(cudaMemcpyAsync(lab_out, d_out, 4 * n, cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaStreamSynchronize(s));
+
+  if (stats) {
+    stats->in_clusters = K;
+    stats->out_clusters = hc.accepted;
+    stats->items = hc.items;
+    stats->splits = hc.splits;
+    stats->peeled = hc.peeled;
+    stats->ni_passes = hc.ni_passes;
+    stats->sw_phases = hc.sw_phases;
+    stats->max_item = (int64_t)hi.max_n;
+    stats->alg_bytes = hc.alg_bytes + 16 * n;
+    stats->ms_membership = tm.ms(0, 1);
+    stats->ms_refine = tm.ms(1, 2);
+    stats->ms_output = tm.ms(2, 3);
+    stats->ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
+            .count();
+  }
+}
+
+Graph *create_from_csr(const int64_t *off, const int32_t *adj, int64_t n, int64_t nnz,
+                       int on_device, cudaStream_t s) {
+  if (n < 0 || n >= (1ll << 31) - 1) fail(WCC_ERR_INVALID, "n must be in [0, 2^31-1)");
+  if (nnz < 0) fail(WCC_ERR_INVALID, "nnz must be >= 0");
+  if (n > 0 && off == nullptr) fail(WCC_ERR_INVALID, "row_off is NULL");
+  if (nnz > 0 && adj == nullptr) fail(WCC_ERR_INVALID, "cols is NULL");
+  std::unique_ptr<Graph> g(new Graph());
+  g->device = current_device();
+  g->n = n;
+  g->nnz = nnz;
+  int64_t *d_off = static_cast<int64_t *>(g->off.ensure(8 * (n + 1)));
+  int32_t *d_adj = static_cast<int32_t *>(g->adj.ensure(4 * std::max<int64_t>(nnz, 1)));
+  cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (n > 0) {
+    WCC_CUDA(cudaMemcpyAsync(d_off, off, 8 * (n + 1), kind, s));
+  } else {
+    WCC_CUDA(cudaMemsetAsync(d_off, 0, 8, s));
+  }
+  if (nnz > 0) WCC_CUDA(cudaMemcpyAsync(d_adj, adj, 4 * nnz, kind, s));
+  // first and last offsets
+  int64_t ends[2] = {0, 0};
+  WCC_CUDA(cudaMemcpyAsync(&ends[0], d_off, 8, cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaMemcpyAsync(&ends[1], d_off + n, 8, cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaStreamSynchronize(s));
+  if (ends[0] != 0 || ends[1] != nnz) fail(WCC_ERR_INVALID, "row_off[0] != 0 or row_off[n] != nnz");
+  if (n > 0) {
+    DevBuf e;
+    unsigned *d_err = static_cast<unsigned *>(e.ensure(4));
+    WCC_CUDA(cudaMemsetAsync(d_err, 0, 4, s));
+    k_validate_csr<<<blocks_for(n * 32), TB, 0, s>>>(d_off, d_adj, n, nnz, d_err); note_launch();
+    WCC_CUDA(cudaGetLastError());
+    unsigned err = read_back(d_err, s);
+    if (err) fail(WCC_ERR_INVALID, "CSR is not a simple symmetric graph with sorted rows");
+  }
+  return g.release();
+}
+
+Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                         int on_device, cudaStream_t s) {
+  if (n < 0 || n >= (1ll << 31) - 1) fail(WCC_ERR_INVALID, "n must be in [0, 2^31-1)");
+  if (m < 0 || 2 * m >= (1ll << 32)) fail(WCC_ERR_INVALID, "m must be in [0, 2^31)");
+  if (m > 0 && (src == nullptr || dst == nullptr)) fail(WCC_ERR_INVALID, "src/dst is NULL");
+  std::unique_ptr<Graph> g(new Graph());
+  g->device = current_device();
+  g->n = n;
+  DevBuf bsrc, bdst, bk, bk2, btemp, bkeep, bpos, bdeg;
+  const int32_t *d_src = src, *d_dst = dst;
+  if (!on_device && m > 0) {
+    int32_t *a = static_cast<int32_t *>(bsrc.ensure(4 * m));
+    int32_t *b = static_cast<int32_t *>(bdst.ensure(4 * m));
+    WCC_CUDA(cudaMemcpyAsync(a, src, 4 * m, cudaMemcpyHostToDevice, s));
+    WCC_CUDA(cudaMemcpyAsync(b, dst, 4 * m, cudaMemcpyHostToDevice, s));
+    d_src = a;
+    d_dst = b;
+  }
+  const int b = std::max(1, bitlen_u64(n > 0 ? (uint64_t)(n - 1) : 0));
+  const int64_t n2 = 2 * m;
+  int64_t *d_off = static_cast<int64_t *>(g->off.ensure(8 * (n + 1)));
+  WCC_CUDA(cudaMemsetAsync(d_off, 0, 8 * (n + 1), s));
+  int64_t nnz = 0;
+  if (m > 0) {
+    uint64_t *k1 = static_cast<uint64_t *>(bk.ensure(8 * n2));
+    uint64_t *k2 = static_cast<uint64_t *>(bk2.ensure(8 * n2));
+    void *temp = btemp.ensure(std::max(radix_temp_bytes(n2), scan_temp_bytes(n + 1)) + 64);
+    unsigned *d_err = static_cast<unsigned *>(bkeep.ensure(4 * (n2 + 1)));
+    WCC_CUDA(cudaMemsetAsync(d_err, 0, 4, s));
+    k_edge_keys<<<blocks_for(m), TB, 0, s>>>(d_src, d_dst, m, n, b, k1, d_err); note_launch();
+    WCC_CUDA(cudaGetLastError());
+    unsigned err = read_back(d_err, s);
+    if (err) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
+    uint64_t *sorted = k1;
+    // valid keys are (u << b) | v < 2^(2b) - 1 (u != v); dropped self-loops
+    // carry all ones, so sorting on the low 2b bits puts them last
+    if (radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, s)) sorted = k2;
+    uint32_t *keep = reinterpret_cast<uint32_t *>(d_err);
+    uint32_t *pos = static_cast<uint32_t *>(bpos.ensure(4 * (n2 + 1)));
+    k_unique_flags<<<blocks_for(n2), TB, 0, s>>>(sorted, n2, keep, ~0ull); note_launch();
+    exclusive_scan_u32(keep, pos, n2, pos + n2, temp, s);
+    uint32_t tot = read_back(pos + n2, s);
+    nnz = tot;
+    int32_t *d_adj = static_cast<int32_t *>(g->adj.ensure(4 * std::max<int64_t>(nnz, 1)));
+    int64_t *deg = static_cast<int64_t *>(bdeg.ensure(8 * (n + 1)));
+    WCC_CUDA(cudaMemsetAsync(deg, 0, 8 * (n + 1), s));
+    k_compact_edges<<<blocks_for(n2), TB, 0, s>>>(sorted, keep, pos, n2, b, d_adj, deg); note_launch();
+    exclusive_scan_i64(deg, d_off, n + 1, nullptr, temp, s);
+    WCC_CUDA(cudaGetLastError());
+  } else {
+    g->adj.ensure(4);
+  }
+  WCC_CUDA(cudaStreamSynchronize(s));
+  g->nnz = nnz;
+  return g.release();
+}
+
+template <typename F>
+int guarded(F &&f) {
+  try {
+    f();
+    g_last_error.clear();
+    return WCC_OK;
+  } catch (const Error &e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return WCC_ERR_OOM;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return WCC_ERR_INTERNAL;
+  }
+}
+
+}  // namespace
+}  // namespace wccg
+
+struct wcc_graph {
+  wccg::Graph *g;
+};
+
+using namespace wccg;
+
+extern "C" {
+
+int wcc_create_graph(const int64_t *row_off, const int32_t *cols, int64_t n, int64_t nnz,
+                     int on_device, void *stream, wcc_graph **out) {
+  return guarded([&] {
+    if (!out) fail(WCC_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    Graph *g = create_from_csr(row_off, cols, n, nnz, on_device, (cudaStream_t)stream);
+    *out = new wcc_graph{g};
+  });
+}
+
+int wcc_create_graph_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                int on_device, void *stream, wcc_graph **out) {
+  return guarded([&] {
+    if (!out) fail(WCC_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    Graph *g = create_from_edges(src, dst, m, n, on_device, (cudaStream_t)stream);
+    *out = new wcc_graph{g};
+  });
+}
+
+int64_t wcc_graph_num_vertices(const wcc_graph *g) { return g ? g->g->n : -1; }
+
+int64_t wcc_graph_nnz(const wcc_graph *g) { return g ? g->g->nnz : -1; }
+
+int wcc_graph_export_csr(const wcc_graph *g, int64_t *row_off, int32_t *cols, int on_device,
+                         void *stream) {
+  return guarded([&] {
+    if (!g || !row_off || (!cols && g->g->nnz > 0)) fail(WCC_ERR_INVALID, "NULL argument");
+    DeviceGuard dg(g->g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    WCC_CUDA(cudaMemcpyAsync(row_off, g->g->off.p, 8 * (g->g->n + 1), k, s));
+    if (g->g->nnz > 0) WCC_CUDA(cudaMemcpyAsync(cols, g->g->adj.p, 4 * g->g->nnz, k, s));
+    WCC_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int wcc_run(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+            int32_t min_size, int32_t mode, int32_t *clustering_out, int on_device, void *stream,
+            wcc_stats *stats) {
+  return guarded([&] {
+    if (!g) fail(WCC_ERR_INVALID, "graph is NULL");
+    std::lock_guard<std::mutex> lk(g->g->run_mutex);
+    DeviceGuard dg(g->g->device);
+    run_impl(g->g, clustering_in, rule, min_size, mode, clustering_out, on_device,
+             (cudaStream_t)stream, stats);
+  });
+}
+
+void wcc_destroy_graph(wcc_graph *g) {
+  if (!g) return;
+  {
+    DeviceGuard *dg = nullptr;
+    try {
+      dg = new DeviceGuard(g->g->device);
+    } catch (...) {
+    }
+    delete g->g;
+    delete dg;
+  }
+  delete g;
+}
+
+int64_t wcc_kernel_launches(void) { return launches_so_far(); }
+
+const char *wcc_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

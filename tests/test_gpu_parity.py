@@ -1,0 +1,180 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work: the refined clustering must be bit-identical to the oracle's
+on the same seeded inputs (both BATCHED and PLAIN schedules, host and device
+buffers).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._helpers import min_labels
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wcc():
+    import paper_2509_02590_gb300 as w
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return w
+
+
+def _oracle(w, rule="log10", num=1, den=1, min_size=None):
+    kind = {"log10": oracle.RULE_LOG10, "log2": oracle.RULE_LOG2, "sqrt": oracle.RULE_SQRT,
+            "linear": oracle.RULE_LINEAR}[rule]
+    off, adj = oracle.build_csr(w.n, w.src, w.dst)
+    out, st = oracle.wcc(w.n, off, adj, w.labels, w.min_size if min_size is None else min_size,
+                         kind, num, den)
+    return out, st, off, adj
+
+
+def _gpu(wcc, w, mode="batched", device=True, rule="log10", num=1, den=1, min_size=None,
+         from_edges=True):
+    ms = w.min_size if min_size is None else min_size
+    if from_edges:
+        g = wcc.WccGraph.from_edges(torch.from_numpy(w.src).cuda(), torch.from_numpy(w.dst).cuda(),
+                                    w.n)
+    else:
+        off, adj = oracle.build_csr(w.n, w.src, w.dst)
+        g = wcc.WccGraph.from_csr(off, adj)
+    with g:
+        if device:
+            out, st = g.run(torch.from_numpy(w.labels).cuda(), min_size=ms, rule=rule, num=num,
+                            den=den, mode=mode, stats=True)
+            out = out.cpu().numpy()
+        else:
+            out, st = g.run(w.labels, min_size=ms, rule=rule, num=num, den=den, mode=mode,
+                            stats=True)
+    return out, st
+
+
+def test_csr_builder_matches_oracle(wcc):
+    w = synth.lfr_like(20000, seed=1)
+    off, adj = oracle.build_csr(w.n, w.src, w.dst)
+    # duplicate and reversed edges plus self-loops in the input are dropped
+    rng = np.random.default_rng(0)
+    extra = rng.integers(0, w.m, 500)
+    src = np.concatenate([w.src, w.dst[extra], np.arange(50, dtype=np.int32)])
+    dst = np.concatenate([w.dst, w.src[extra], np.arange(50, dtype=np.int32)])
+    with wcc.WccGraph.from_edges(src, dst, w.n) as g:
+        goff, gadj = g.csr()
+    assert np.array_equal(goff, off) and np.array_equal(gadj, adj)
+
+
+def test_planted_1k_all_modes(wcc):
+    w = synth.planted_1k(0)
+    ref, rst, _, _ = _oracle(w)
+    for mode in ("batched", "plain"):
+        for device in (True, False):
+            out, st = _gpu(wcc, w, mode=mode, device=device)
+            assert np.array_equal(out, ref), (mode, device)
+            assert st["out_clusters"] == rst["out_clusters"]
+            assert st["splits"] == rst["splits"]
+            assert st["peeled"] == rst["peeled"]
+
+
+def test_lfr_100k_full(wcc):
+    w = synth.lfr_like(100_000, seed=0)
+    ref, rst, _, _ = _oracle(w)
+    out, st = _gpu(wcc, w)
+    assert np.array_equal(out, ref)
+    assert st["in_clusters"] == rst["in_clusters"]
+    assert st["out_clusters"] == rst["out_clusters"]
+
+
+def test_lfr_plain_equals_batched(wcc):
+    w = synth.lfr_like(30_000, seed=2)
+    ref, _, _, _ = _oracle(w)
+    a, _ = _gpu(wcc, w, mode="batched")
+    b, _ = _gpu(wcc, w, mode="plain", from_edges=False)
+    assert np.array_equal(a, ref) and np.array_equal(b, ref)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_instances(wcc, seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(200, 3000))
+    k = int(rng.integers(2, 40))
+    lab = rng.integers(0, k, n).astype(np.int32)
+    lab[rng.random(n) < 0.1] = -1
+    src, dst = [], []
+    for c in range(k):
+        vs = np.nonzero(lab == c)[0]
+        if len(vs) < 2:
+            continue
+        a, b = synth.random_gnp(len(vs), float(rng.uniform(0.02, 0.4)), rng)
+        src.append(vs[a]); dst.append(vs[b])
+    a, b = synth.random_gnp(n, 3.0 / n, rng)
+    src.append(a); dst.append(b)
+    s, d = synth.graphs._dedup(n, np.concatenate(src), np.concatenate(dst))
+    w = synth.Workload("rand", n, s, d, lab, int(rng.integers(2, 8)))
+    ref, _, _, _ = _oracle(w)
+    out, _ = _gpu(wcc, w)
+    assert np.array_equal(out, ref)
+
+
+@pytest.mark.parametrize("rule,num,den", [("log2", 1, 1), ("sqrt", 1, 1), ("linear", 1, 20)])
+def test_other_rules(wcc, rule, num, den):
+    w = synth.lfr_like(8000, seed=4)
+    ref, _, _, _ = _oracle(w, rule, num, den)
+    out, _ = _gpu(wcc, w, rule=rule, num=num, den=den)
+    assert np.array_equal(out, ref)
+
+
+def test_dc_planted_small(wcc):
+    w = synth.dc_planted(200_000, 2_000_000, seed=5, size_max=5000)
+    ref, _, _, _ = _oracle(w)
+    out, _ = _gpu(wcc, w)
+    assert np.array_equal(out, ref)
+
+
+def test_edge_cases(wcc):
+    n, eu, ev = synth.tiny_family("complete", 6)
+    off, adj = oracle.build_csr(n, eu, ev)
+    with wcc.WccGraph.from_csr(off, adj) as g:
+        assert np.all(g.run(np.full(n, -1, np.int32)) == -1)           # no clusters
+        assert np.all(g.run(np.zeros(n, np.int32)) == 0)               # one clique
+        assert np.all(g.run(np.arange(n, dtype=np.int32)) == -1)       # singletons
+        assert np.all(g.run(np.zeros(n, np.int32), min_size=7) == -1)  # too small
+        assert np.all(g.run(np.zeros(n, np.int32), min_size=0) == 0)   # min_size < 2 acts as 2
+        big = np.full(n, 2**31 - 1, np.int32)
+        assert np.all(g.run(big) == 0)                                 # arbitrary label values
+        with pytest.raises(wcc.WccError):
+            g.run(np.full(n, -5, np.int32))                            # labels below -1
+    # empty graph with clusters: everything is a singleton after CCR
+    with wcc.WccGraph.from_edges(np.zeros(0, np.int32), np.zeros(0, np.int32), 10) as g:
+        assert np.all(g.run(np.zeros(10, np.int32)) == -1)
+
+
+def test_invalid_graphs_rejected(wcc):
+    with pytest.raises(wcc.WccError):   # asymmetric
+        wcc.WccGraph.from_csr(np.array([0, 1, 1], np.int64), np.array([1], np.int32))
+    with pytest.raises(wcc.WccError):   # self-loop
+        wcc.WccGraph.from_csr(np.array([0, 1], np.int64), np.array([0], np.int32))
+    with pytest.raises(wcc.WccError):   # id out of range
+        wcc.WccGraph.from_edges(np.array([0], np.int32), np.array([5], np.int32), 3)
+
+
+def test_hand_traced_items(wcc):
+    # two K5 joined by one edge, one cluster of 10: T(10) = 1, cut 1 -> split
+    eu, ev = [], []
+    for base in (0, 5):
+        for i in range(5):
+            for j in range(i + 1, 5):
+                eu.append(base + i); ev.append(base + j)
+    eu.append(4); ev.append(5)
+    w = synth.Workload("k5k5", 10, np.array(eu, np.int32), np.array(ev, np.int32),
+                       np.zeros(10, np.int32), 2)
+    out, _ = _gpu(wcc, w)
+    assert out.tolist() == [0] * 5 + [1] * 5
+
+
+def test_min_labels_consistent(wcc):
+    w = synth.lfr_like(5000, seed=7)
+    ref, _, _, _ = _oracle(w)
+    out, _ = _gpu(wcc, w)
+    assert np.array_equal(min_labels(out), min_labels(ref))
