@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 
@@ -200,6 +201,22 @@ __global__ void k_keep(const int64_t *__restrict__ cstart, int64_t K, int min_si
   }
 }
 
+// Sort keys putting kept clusters first, larger ones earlier (longest work
+// first); unkept clusters get the largest key.
+__global__ void k_size_keys(const int64_t *__restrict__ cstart, const uint32_t *__restrict__ keep,
+                            int64_t K, uint32_t max_n, uint32_t *keys, uint32_t *vals) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= K) return;
+  uint32_t sz = (uint32_t)(cstart[c + 1] - cstart[c]);
+  keys[c] = keep[c] ? max_n - sz : max_n + 1;
+  vals[c] = (uint32_t)c;
+}
+
+__global__ void k_invert(const uint32_t *__restrict__ order, int64_t nkept, uint32_t *qidx) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nkept) qidx[order[i]] = (uint32_t)i;
+}
+
 __global__ void k_seed(const int64_t *__restrict__ cstart, const uint32_t *__restrict__ keep,
                        const uint32_t *__restrict__ qidx, int64_t K, int64_t skip, QSlot *ring,
                        uint64_t cap) {
@@ -289,6 +306,18 @@ uint64_t wait_limit_ns() {
   return (uint64_t)ms * 1000000ull;
 }
 
+// Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
+// largest a CTA can opt into, one CTA per SM).  Items whose working set is
+// larger use a global slab.
+size_t refine_smem_bytes_config(int device) {
+  const char *e = getenv("WCC_SMEM_KB");
+  long long kb = e ? atoll(e) : (1ll << 30);
+  long long mx = (long long)(refine_smem_max_bytes(device) / 1024);
+  if (kb < 16) kb = 16;
+  if (kb > mx) kb = mx;
+  return (size_t)kb * 1024;
+}
+
 template <typename T>
 T read_back(const T *dev, cudaStream_t s) {
   T h;
@@ -297,12 +326,33 @@ T read_back(const T *dev, cudaStream_t s) {
   return h;
 }
 
+// Writes the per-item profile of the last refinement as CSV (appending).
+void dump_item_profile(const RefineParams &p, const char *path, cudaStream_t s) {
+  unsigned cnt = read_back(p.prof_count, s);
+  if (cnt > p.prof_cap) cnt = p.prof_cap;
+  std::vector<ItemProf> h(cnt);
+  if (cnt) {
+    WCC_CUDA(cudaMemcpyAsync(h.data(), p.prof, sizeof(ItemProf) * cnt, cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaStreamSynchronize(s));
+  }
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "seq,n,E,nalive,passes,nsv,outcome,smid,slab,top,load,extract,ccr,peel,cc,contract,"
+             "sw,out,t_begin,p1_cycles,p1_pick,p1_steps,p1_scan\n");
+  for (const ItemProf &q : h)
+    fprintf(f, "%u,%d,%d,%d,%d,%d,%d,%d,%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%lld,%lld,%lld,%lld,%lld\n",
+            q.seq, q.n, q.E, q.nalive, q.passes, q.nsv, q.outcome, q.smid, q.slab, q.top,
+            q.dt[0], q.dt[1], q.dt[2], q.dt[3], q.dt[4], q.dt[5], q.dt[6], q.dt[7], q.t_begin,
+            q.dbg[0], q.dbg[1], q.dbg[2], q.dbg[3]);
+  fclose(f);
+}
+
 enum Ws {
   W_KEYS, W_VALS, W_KEYS2, W_VALS2, W_TEMP, W_HEAD, W_HIDX, W_CSTART, W_PDEG, W_KEEP, W_QIDX,
   W_POOL, W_SLOT, W_LMIN, W_RING, W_CTR, W_SLAB, W_INFO, W_OUT, W_IN, W_FLAG, W_RANK, W_DG,
-  W_COUNT
+  W_OK1, W_OV1, W_OK2, W_OV2, W_COUNT
 };
-static_assert(W_COUNT <= 24, "workspace slots");
+static_assert(W_COUNT <= 32, "workspace slots");
 
 struct Timer {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -413,11 +463,26 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     WCC_CUDA(cudaGetLastError());
     hi = read_back(info, s);
     nkept = (int64_t)hi.kept;
+    if (nkept > 1) {
+      // queue order: largest input clusters first (qidx = rank by size)
+      uint32_t *ok1 = static_cast<uint32_t *>(ws[W_OK1].ensure(4 * K));
+      uint32_t *ov1 = static_cast<uint32_t *>(ws[W_OV1].ensure(4 * K));
+      uint32_t *ok2 = static_cast<uint32_t *>(ws[W_OK2].ensure(4 * K));
+      uint32_t *ov2 = static_cast<uint32_t *>(ws[W_OV2].ensure(4 * K));
+      k_size_keys<<<blocks_for(K), TB, 0, s>>>(cstart, keep, K, (uint32_t)hi.max_n, ok1, ov1);
+      note_launch();
+      uint32_t *ov = ov1;
+      if (radix_sort_pairs_u32(ok1, ov1, ok2, ov2, K, bitlen_u64(hi.max_n + 1), temp, s)) ov = ov2;
+      k_invert<<<blocks_for(nkept), TB, 0, s>>>(ov, nkept, qidx);
+      note_launch();
+      WCC_CUDA(cudaGetLastError());
+    }
   }
 
   // ---- queue, pool, slots
   const int dev = g->device;
-  const int max_ctas = refine_max_ctas(dev);
+  const size_t smem_bytes = refine_smem_bytes_config(dev);
+  const int max_ctas = refine_max_ctas(dev, smem_bytes);
   const int grid = max_ctas;
   const uint64_t cap = (uint64_t)n + 2ull * grid + 1024;
   int32_t *pool = static_cast<int32_t *>(ws[W_POOL].ensure(4 * std::max<int64_t>(n - skip, 1)));
@@ -444,7 +509,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
   // ---- refinement
   if (nkept > 0) {
     size_t need = item_workspace_bytes((int64_t)hi.max_n, (int64_t)hi.max_dsum);
-    size_t slab_bytes = need > refine_smem_bytes() ? ((need + 255) & ~(size_t)255) : 256;
+    size_t slab_bytes = need > smem_bytes ? ((need + 255) & ~(size_t)255) : 256;
     RefineParams p{};
     p.off = g->off.as<int64_t>();
     p.adj = g->adj.as<int32_t>();
@@ -460,8 +525,19 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     p.rule_den = r.den;
     p.min_size = min_size;
     p.wait_limit_ns = wait_limit_ns();
-    p.smem_bytes = refine_smem_bytes();
+    p.smem_bytes = smem_bytes;
     p.slab_bytes = slab_bytes;
+    // optional per-item profile (WCC_PROFILE_ITEMS=<csv path>)
+    const char *prof_path = getenv("WCC_PROFILE_ITEMS");
+    DevBuf prof_buf;
+    const unsigned prof_cap = 1u << 20;
+    if (prof_path && *prof_path) {
+      char *pb = static_cast<char *>(prof_buf.ensure(sizeof(ItemProf) * prof_cap + 64));
+      p.prof = reinterpret_cast<ItemProf *>(pb + 64);
+      p.prof_count = reinterpret_cast<unsigned *>(pb);
+      p.prof_cap = prof_cap;
+      WCC_CUDA(cudaMemsetAsync(pb, 0, 64, s));
+    }
     if (mode == WCC_MODE_BATCHED) {
       p.slab = static_cast<char *>(ws[W_SLAB].ensure(slab_bytes * (size_t)grid));
       p.single_item = 0;
@@ -480,6 +556,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
         }
       }
     }
+    if (p.prof) dump_item_profile(p, prof_path, s);
   }
   tm.mark(2, s);
   RunCounters hc{};

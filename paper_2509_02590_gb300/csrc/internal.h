@@ -61,7 +61,7 @@ struct Graph {
   DevBuf adj;  // int32 [nnz]
   std::mutex run_mutex;  // wcc_run calls on one graph are serialised
   // per-run workspace, kept between runs
-  DevBuf ws[24];
+  DevBuf ws[32];
 };
 
 // ---- refine.cu -------------------------------------------------------------
@@ -91,6 +91,16 @@ struct RunCounters {
   long long alg_bytes;         // bytes of adjacency + slot gathers actually read
 };
 
+// Optional per-item profile record (phase durations in SM cycles: load,
+// extraction, CCR, peel, CC, contraction, Stoer-Wagner, output).
+struct ItemProf {
+  unsigned seq;
+  int n, E, nalive, passes, nsv, outcome, smid, slab, top;
+  unsigned dt[8];
+  long long t_begin;
+  long long dbg[4];  // first contraction pass: loop cycles, pick cycles, steps, scan cycles
+};
+
 struct RefineParams {
   const int64_t *off;
   const int32_t *adj;
@@ -111,14 +121,19 @@ struct RefineParams {
   size_t smem_bytes;          // dynamic shared memory per CTA
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
+  ItemProf *prof;             // optional per-item profile (NULL = off)
+  unsigned prof_cap;
+  unsigned *prof_count;
 };
 
 // Bytes of working memory an item of n vertices and at most e local
 // directed edges needs.
 size_t item_workspace_bytes(int64_t n, int64_t e);
 int refine_block_threads();
-size_t refine_smem_bytes();
-int refine_max_ctas(int device);
+size_t refine_smem_max_bytes(int device);
+// CTAs of the refinement kernel resident on the whole device with
+// smem_bytes of dynamic shared memory each.
+int refine_max_ctas(int device, size_t smem_bytes);
 void launch_refine(const RefineParams &p, int grid, bool cooperative, cudaStream_t s);
 
 }  // namespace wccg

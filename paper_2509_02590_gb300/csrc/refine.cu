@@ -1,19 +1,22 @@
 // refine.cu -- the refinement kernel: one CTA processes one work item at a
 // time (an input cluster, or a part produced by an earlier split), entirely
 // in on-chip shared memory when the item fits, else in a per-CTA slab of
-// global memory (L2-resident for the sizes that need it).
+// global memory.
 //
 // Per item (paper: Algorithm 1 for input clusters, then Algorithm 3 with a
 // peel and a connectivity check in front of the cut):
 //   1. extraction of the induced subgraph G[S] (Algorithm 1 / 3: E_c = edges
 //      with both ends in V_c) into a local CSR, local id = rank of the global
-//      id in S, by warp-per-vertex scans of the global adjacency with one
-//      8-byte gather of slot[u] = (item << 32 | local id) per neighbour;
+//      id in S: one flat, load-balanced pass over all adjacency entries of
+//      the members with an 8-byte gather of slot[u] = (item << 32 | local id)
+//      per entry; local ids are 16-bit when the item has < 65535 vertices;
 //   2. input clusters only: connected components (CCR); each component with
 //      at least min_size vertices is queued, or refinement continues in place
 //      when the cluster is one component;
 //   3. round-synchronous peel of vertices with degree <= T(n);
-//   4. connected components; more than one -> queue each large component;
+//   4. if the peel removed anything: connected components; more than one ->
+//      queue each large component (an item arrives connected, so without a
+//      peel the check is skipped);
 //   5. Nagamochi-Ibaraki contraction with k = T+1: maximum-adjacency passes
 //      (keys capped at k, ties to the smallest id) merging every edge whose
 //      key reaches k, until one super-vertex (accept: min cut > T) or a pass
@@ -33,32 +36,58 @@ namespace {
 
 constexpr int RB = 256;        // threads per CTA
 constexpr int RW = RB / 32;    // warps per CTA
-constexpr size_t SMEM_BYTES = 56 * 1024;
-constexpr uint32_t SLOT_NONE_HI = 0xffffffffu;
+constexpr size_t SMEM_MAX_BYTES = 227 * 1024;  // opt-in limit per CTA
+
+// Dynamic shared memory of a refinement CTA.  Item code instantiated for
+// shared memory derives every pointer from this symbol, so the compiler
+// knows their address space and uses shared-memory instructions instead of
+// generic ones.
+extern __shared__ __align__(16) char wcc_dyn_smem[];
+
+// Contraction passes keep every not-yet-added super-vertex in the bucket of
+// its (capped) key: KB_LEVELS bitmaps over local ids plus one summary bit per
+// bitmap word, so "largest key, then smallest id" is the highest non-empty
+// bucket's lowest set bit.  Caps above KB_LEVELS-1 use the linear argmax.
+constexpr int KB_LEVELS = 16;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-// Working memory of one item: see carve().
-__host__ __device__ inline size_t ws_fixed_bytes(int64_t n) {
-  size_t b = 0;
-  b += align16(4 * (size_t)n);        // gid
-  b += align16(4 * (size_t)(n + 1));  // off
-  b += 8 * align16(4 * (size_t)(n + 1));  // A..H
-  b += align16(8 * (size_t)n);        // pk
-  b += 3 * align16((size_t)n);        // alive, flag, side
-  return b;
+__host__ __device__ inline int bm_words(int64_t n) { return (int)((n + 31) / 32); }
+__host__ __device__ inline int bm_sum_words(int64_t n) { return (bm_words(n) + 31) / 32; }
+__host__ __device__ inline size_t bucket_bitmap_bytes(int64_t n) {
+  return align16(4 * (size_t)KB_LEVELS * (size_t)(bm_words(n) + bm_sum_words(n)));
 }
 
+// Working memory of one item of n vertices and at most d local adjacency
+// entries (d = sum of the members' global degrees); see carve().
+template <typename IT>
+__host__ __device__ inline size_t ws_bytes(int64_t n, int64_t d) {
+  size_t b = 0;
+  b += align16(4 * (size_t)n);              // gid
+  b += align16(4 * (size_t)(n + 1));        // off
+  b += 6 * align16(4 * (size_t)(n + 1));    // A, B, C, D, G, H
+  b += align16(8 * (size_t)(n + 1));        // E and F (one int64 array during extraction)
+  b += 4 * align16((size_t)n);              // alive, flag, side, kst
+  b += bucket_bitmap_bytes(n);              // key buckets
+  b += align16(4 * (size_t)((d + 31) / 32 + 1));  // contraction marks, one bit per entry
+  b += align16(sizeof(IT) * (size_t)d);     // local adjacency
+  return b + 64;
+}
+
+template <typename IT>
 struct Mem {
   int32_t *gid, *off, *A, *B, *C, *D, *E, *F, *G, *H;
-  unsigned long long *pk;
+  int64_t *wide;       // E..F viewed as int64[n+1]
   uint8_t *alive, *flag, *side;
-  int32_t *adj;
-  int64_t adj_cap;
+  uint8_t *kst;        // first contraction pass: capped key, or 255 once added / dead
+  uint32_t *bm, *bms;  // bucket bitmaps [KB_LEVELS][W], summaries [KB_LEVELS][S]
+  int W, S;
+  uint32_t *ebits;     // one bit per local adjacency entry
+  IT *adj;
 };
 
-__device__ inline Mem carve(char *base, size_t bytes, int n) {
-  Mem m;
+template <typename IT>
+__device__ __forceinline__ Mem<IT> carve(char *base, int n, int64_t d) {
+  Mem<IT> m;
   char *p = base;
   auto take = [&](size_t b) { char *r = p; p += align16(b); return r; };
   m.gid = (int32_t *)take(4 * (size_t)n);
@@ -67,16 +96,21 @@ __device__ inline Mem carve(char *base, size_t bytes, int n) {
   m.B = (int32_t *)take(4 * (size_t)(n + 1));
   m.C = (int32_t *)take(4 * (size_t)(n + 1));
   m.D = (int32_t *)take(4 * (size_t)(n + 1));
-  m.E = (int32_t *)take(4 * (size_t)(n + 1));
-  m.F = (int32_t *)take(4 * (size_t)(n + 1));
   m.G = (int32_t *)take(4 * (size_t)(n + 1));
   m.H = (int32_t *)take(4 * (size_t)(n + 1));
-  m.pk = (unsigned long long *)take(8 * (size_t)n);
+  m.wide = (int64_t *)take(8 * (size_t)(n + 1));
+  m.E = (int32_t *)m.wide;
+  m.F = m.E + (n + 1);
   m.alive = (uint8_t *)take((size_t)n);
   m.flag = (uint8_t *)take((size_t)n);
   m.side = (uint8_t *)take((size_t)n);
-  m.adj = (int32_t *)p;
-  m.adj_cap = (int64_t)((base + bytes - p) / 4);
+  m.kst = (uint8_t *)take((size_t)n);
+  m.W = bm_words(n);
+  m.S = bm_sum_words(n);
+  m.bm = (uint32_t *)take(bucket_bitmap_bytes(n));
+  m.bms = m.bm + (size_t)KB_LEVELS * m.W;
+  m.ebits = (uint32_t *)take(4 * (size_t)((d + 31) / 32 + 1));
+  m.adj = (IT *)take(sizeof(IT) * (size_t)d);
   return m;
 }
 
@@ -87,13 +121,26 @@ struct Sh {
   unsigned long long seq;
   Item item;
   int go;
-  int32_t i0, i1, i2, i3;
-  long long l0;
+  int32_t i0;
   unsigned long long u0;
   int32_t ntouched;
   int32_t contracted;
+  int32_t changed;
   int32_t sw_s, sw_t, sw_cut;
+  // per-item profile (only when RefineParams::prof is set)
+  long long ts[9];
+  long long dbg[4];
+  int32_t used_slab, pf_E, pf_nalive, pf_passes, pf_nsv;
 };
+
+// Outcome of one item.
+enum : int { OUT_ERROR = -1, OUT_DROPPED = 0, OUT_CCR_SPLIT = 1, OUT_CC_SPLIT = 2,
+             OUT_ACCEPT = 3, OUT_CUT_SPLIT = 4 };
+
+// Cycle stamp k of the per-item profile (thread 0; no-op unless enabled).
+__device__ __forceinline__ void prof_stamp(const RefineParams &P, Sh &sh, int k) {
+  if (P.prof && threadIdx.x == 0) sh.ts[k] = clock64();
+}
 
 // ---- small device helpers ----------------------------------------------------
 
@@ -103,8 +150,7 @@ __device__ __forceinline__ void add_ll(long long *p, long long v) {
 }
 
 // Criterion threshold T(n) (Section 2, criterion f(n)): the largest integer
-// with cut <= T(n) <=> cut <= f(n) for integer cuts.  Written here
-// independently of any host code.
+// with cut <= T(n) <=> cut <= f(n) for integer cuts.
 __device__ int64_t threshold_of(int kind, int64_t num, int64_t den, int64_t n) {
   if (n < 1) return -1;
   int64_t t = 0, p = 1;
@@ -180,30 +226,166 @@ __device__ long long block_sum_ll(long long v, Sh &sh) {
 }
 
 // ---- connected components of the alive vertices ----------------------------
-// parent = B; returns the number of components; B[i] = smallest alive local
-// id of i's component (or -1 for dead vertices).
-__device__ int components(const Mem &m, int n, Sh &sh) {
-  for (int i = threadIdx.x; i < n; i += RB) m.B[i] = m.alive[i] ? i : -1;
-  __syncthreads();
-  // warp per vertex: hook every alive edge (i, j), i < j
+// Hook-and-shortcut rounds: every alive edge (i, j) lowers the label of the
+// larger of f[i], f[j] to the smaller one (atomicMin), then every label is
+// shortcut to its label's label until stable; rounds repeat until neither
+// step changes anything.  Labels only decrease and stay ids of the same
+// component, so the fixpoint labels each component with its smallest id.
+// f[i] = that id (-1 for dead vertices; f defaults to B); returns the number
+// of components.  With emask, only the adjacency entries whose bit is set
+// count as edges (an undirected edge may be marked on either of its two
+// entries).
+template <typename IT>
+__device__ __forceinline__ int components(const Mem<IT> &m, int n, Sh &sh, int32_t *f = nullptr,
+                          const uint32_t *emask = nullptr) {
+  if (f == nullptr) f = m.B;
+  volatile int32_t *vf = f;
+  for (int i = threadIdx.x; i < n; i += RB) f[i] = m.alive[i] ? i : -1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int round = 0; round <= n; ++round) {
+    if (threadIdx.x == 0) sh.changed = 0;
+    __syncthreads();
+    int changed = 0;
+    for (int i = threadIdx.x; i < n; i += RB) {
+      if (!m.alive[i]) continue;
+      const int b = m.off[i], e = m.off[i + 1];
+      if (e - b > 32) continue;
+      for (int q = b; q < e; ++q) {
+        const int j = m.adj[q];
+        if (emask) {
+          if (!(emask[q >> 5] & (1u << (q & 31)))) continue;
+        } else if (j <= i || !m.alive[j]) {
+          continue;
+        }
+        const int a = vf[i], c = vf[j];
+        if (a != c) {
+          const int hi = a > c ? a : c, lo = a > c ? c : a;
+          if (atomicMin(&f[hi], lo) > lo) changed = 1;
+        }
+      }
+    }
+    for (int i = warp; i < n; i += RW) {
+      const int b = m.off[i], e = m.off[i + 1];
+      if (!m.alive[i] || e - b <= 32) continue;
+      for (int q = b + lane; q < e; q += 32) {
+        const int j = m.adj[q];
+        if (emask) {
+          if (!(emask[q >> 5] & (1u << (q & 31)))) continue;
+        } else if (j <= i || !m.alive[j]) {
+          continue;
+        }
+        const int a = vf[i], c = vf[j];
+        if (a != c) {
+          const int hi = a > c ? a : c, lo = a > c ? c : a;
+          if (atomicMin(&f[hi], lo) > lo) changed = 1;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += RB) {
+      if (!m.alive[i]) continue;
+      int x = vf[i];
+      int y = vf[x];
+      while (y != x) {
+        x = y;
+        y = vf[x];
+      }
+      if (vf[i] != x) {
+        vf[i] = x;
+        changed = 1;
+      }
+    }
+    if (changed) sh.changed = 1;
+    __syncthreads();
+    if (!sh.changed) break;
+  }
+  int roots = 0;
+  for (int i = threadIdx.x; i < n; i += RB) roots += (m.alive[i] && f[i] == i);
+  return block_sum_int(roots, sh);
+}
+
+// ---- connected components (Afforest-style) ---------------------------------
+// Union-find over the alive vertices (uf, root = smallest id): every vertex
+// first links along its first two alive neighbours, the sets are
+// compressed, and then only vertices outside the set of the smallest alive
+// vertex process the rest of their rows (an edge with one end in that set is
+// seen from its other end; an edge with both ends in it is already inside
+// one set).  The result is exactly the connected components, with far fewer
+// unions than hooking every edge.  cur is per-vertex scratch.
+template <typename IT>
+__device__ __forceinline__ void afforest(const Mem<IT> &m, int n, int32_t *uf, int32_t *cur,
+                                         Sh &sh) {
+  for (int i = threadIdx.x; i < n; i += RB) {
+    uf[i] = i;
+    cur[i] = m.off[i];
+  }
+  if (threadIdx.x == 0) sh.i0 = n;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RB)
+    if (m.alive[i]) { atomicMin(&sh.i0, i); break; }
+  // sampling: two alive neighbours per vertex
+  for (int r = 0; r < 2; ++r) {
+    for (int i = threadIdx.x; i < n; i += RB) {
+      if (!m.alive[i]) continue;
+      const int e = m.off[i + 1];
+      int q = cur[i];
+      for (; q < e; ++q) {
+        const int j = m.adj[q];
+        if (m.alive[j]) {
+          uf_union(uf, i, j);
+          ++q;
+          break;
+        }
+      }
+      cur[i] = q;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += RB)
+    if (m.alive[i]) uf[i] = uf_find(uf, i);
+  __syncthreads();
+  const int i0 = sh.i0;
+  const int giant = i0 < n ? uf_find(uf, i0) : -1;
+  // every vertex outside the giant set processes the rest of its row
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < n; i += RB) {
+    if (!m.alive[i]) continue;
+    const int e = m.off[i + 1];
+    if (e - cur[i] > 64 || uf_find(uf, i) == giant) continue;
+    for (int q = cur[i]; q < e; ++q) {
+      const int j = m.adj[q];
+      if (m.alive[j]) uf_union(uf, i, j);
+    }
+  }
   for (int i = warp; i < n; i += RW) {
     if (!m.alive[i]) continue;
-    for (int e = m.off[i] + lane; e < m.off[i + 1]; e += 32) {
-      int j = m.adj[e];
-      if (j > i && m.alive[j]) uf_union(m.B, i, j);
+    const int e = m.off[i + 1];
+    if (e - cur[i] <= 64 || uf_find(uf, i) == giant) continue;
+    for (int q = cur[i] + lane; q < e; q += 32) {
+      const int j = m.adj[q];
+      if (m.alive[j]) uf_union(uf, i, j);
     }
   }
   __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RB)
+    if (m.alive[i]) uf[i] = uf_find(uf, i);
+  __syncthreads();
+}
+
+// Connected components of the alive vertices by afforest(): f[i] = smallest
+// alive id of i's component (-1 if dead); returns the number of components.
+template <typename IT>
+__device__ __forceinline__ int components_af(const Mem<IT> &m, int n, int32_t *f, int32_t *cur,
+                                             Sh &sh) {
+  afforest(m, n, f, cur, sh);
   int roots = 0;
   for (int i = threadIdx.x; i < n; i += RB) {
-    if (!m.alive[i]) continue;
-    int r = uf_find(m.B, i);
-    roots += (r == i);
+    if (!m.alive[i]) {
+      f[i] = -1;
+      continue;
+    }
+    roots += f[i] == i;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += RB)
-    if (m.alive[i]) m.B[i] = uf_find(m.B, i);
   __syncthreads();
   return block_sum_int(roots, sh);
 }
@@ -212,7 +394,8 @@ __device__ int components(const Mem &m, int n, Sh &sh) {
 // tag[i] in [0, n) names the child of local vertex i (-1: none).  Every tag
 // with at least min_size members becomes a new queue item whose vertex list
 // (ascending) is written into the parent's pool range.  Uses C, D, E, F.
-__device__ void emit_children(const RefineParams &P, const Mem &m, const int32_t *tag, int n,
+template <typename IT>
+__device__ __forceinline__ void emit_children(const RefineParams &P, const Mem<IT> &m, const int32_t *tag, int n,
                               int64_t vbeg, Sh &sh) {
   int32_t *cnt = m.C, *cidx = m.D, *cbase = m.E, *run = m.F;
   for (int t = threadIdx.x; t < n; t += RB) cnt[t] = 0;
@@ -281,24 +464,28 @@ __device__ void emit_children(const RefineParams &P, const Mem &m, const int32_t
 
 // ---- maximum-adjacency machinery -----------------------------------------
 // The current super-vertices are the ids X with grp[X] == X among alive
-// vertices.  group_members() lists them (pos[X] = list index, ascending) and
-// groups their members: members of the super-vertex at list index j are
-// D[C[j] .. C[j+1]).  Returns the count.  Uses C, D, G (pos), H (temp).
-__device__ int group_members(const Mem &m, const int32_t *grp, int n, Sh &sh) {
-  int32_t *pos = m.G, *gof = m.C, *mem = m.D, *fill = m.H;
-  for (int i = threadIdx.x; i < n; i += RB) pos[i] = (m.alive[i] && grp[i] == i) ? 1 : 0;
-  __syncthreads();
-  int nsv = block_scan_array(pos, n, sh);
-  for (int j = threadIdx.x; j <= nsv; j += RB) gof[j] = 0;
+// vertices.  group_members() counts and lists their members: members of X
+// are D[C[X] .. C[X+1]) (C indexed by id), and G[0..nsv) lists the
+// super-vertices in ascending order.  Uses C, D, G, H; returns nsv.
+template <typename IT>
+__device__ __forceinline__ int group_members(const Mem<IT> &m, const int32_t *grp, int n, Sh &sh) {
+  int32_t *gof = m.C, *mem = m.D, *svl = m.G, *tmp = m.H;
+  for (int i = threadIdx.x; i <= n; i += RB) gof[i] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += RB)
-    if (m.alive[i]) atomicAdd(&gof[pos[grp[i]]], 1);
+    if (m.alive[i]) atomicAdd(&gof[grp[i]], 1);
   __syncthreads();
-  block_scan_array(gof, nsv + 1, sh);
-  for (int j = threadIdx.x; j < nsv; j += RB) fill[j] = gof[j];
+  block_scan_array(gof, n + 1, sh);
+  for (int i = threadIdx.x; i < n; i += RB) tmp[i] = gof[i];
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += RB)
-    if (m.alive[i]) mem[atomicAdd(&fill[pos[grp[i]]], 1)] = i;
+    if (m.alive[i]) mem[atomicAdd(&tmp[grp[i]], 1)] = i;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RB) tmp[i] = (m.alive[i] && grp[i] == i) ? 1 : 0;
+  __syncthreads();
+  const int nsv = block_scan_array(tmp, n, sh);
+  for (int i = threadIdx.x; i < n; i += RB)
+    if (m.alive[i] && grp[i] == i) svl[tmp[i]] = i;
   __syncthreads();
   return nsv;
 }
@@ -307,21 +494,49 @@ __device__ __forceinline__ unsigned long long pack_key(int key, int id) {
   return ((unsigned long long)(unsigned)key << 32) | (unsigned)(~(unsigned)id);
 }
 
-// One maximum-adjacency ordering over the current super-vertices, run by
-// warp 0 (the other warps wait at the closing barrier).  kcap > 0: keys
-// capped at kcap and every edge X-Y whose key reaches kcap is merged into
-// nrep (the contraction pass); kcap == 0: exact keys (a Stoer-Wagner phase),
-// reporting the last two super-vertices s, t and the cut of the phase.
-// Uses E (acc), F (key), H (touched), pk, flag (in A).
-__device__ void ma_ordering(const Mem &m, const int32_t *grp, int32_t *nrep, int nsv, int kcap,
-                            Sh &sh) {
-  int32_t *acc = m.E, *key = m.F, *touched = m.H, *pos = m.G;
-  for (int j = threadIdx.x; j < nsv; j += RB) {
-    int X = m.D[m.C[j]];  // any member; its group id
-    X = grp[X];
-    m.pk[j] = pack_key(0, X);
+// Adds the weights of super-vertex X's edges to every not-yet-added
+// neighbour Y: acc[Y] += w(X, Y); each Y reached is listed once in touched.
+// Warp 0 only.
+template <typename IT>
+__device__ __forceinline__ void scan_super_vertex(const Mem<IT> &m, const int32_t *grp, int X,
+                                                  Sh &sh) {
+  const int lane = threadIdx.x & 31;
+  int32_t *acc = m.E, *touched = m.H;
+  const int mb = m.C[X], me = m.C[X + 1];
+  if (me - mb == 1) {
+    const int i = m.D[mb];
+    for (int e = m.off[i] + lane; e < m.off[i + 1]; e += 32) {
+      const int j = m.adj[e];
+      if (!m.alive[j]) continue;
+      const int Y = grp[j];
+      if (Y == X || m.flag[Y]) continue;
+      if (atomicAdd(&acc[Y], 1) == 0) touched[atomicAdd(&sh.ntouched, 1)] = Y;
+    }
+  } else {
+    for (int q = mb + lane; q < me; q += 32) {
+      const int i = m.D[q];
+      for (int e = m.off[i]; e < m.off[i + 1]; ++e) {
+        const int j = m.adj[e];
+        if (!m.alive[j]) continue;
+        const int Y = grp[j];
+        if (Y == X || m.flag[Y]) continue;
+        if (atomicAdd(&acc[Y], 1) == 0) touched[atomicAdd(&sh.ntouched, 1)] = Y;
+      }
+    }
   }
-  __syncthreads();
+}
+
+// One maximum-adjacency ordering over the current super-vertices with a
+// linear argmax, run by warp 0.  kcap > 0: keys capped at kcap and every
+// edge X-Y whose key reaches kcap is merged into nrep (a contraction pass);
+// kcap == 0: exact keys (a Stoer-Wagner phase), reporting the last two
+// super-vertices s, t and the cut of the phase.  Needs group_members() and
+// zeroed E (acc), F (key), flag (in A).  touched (H) is reused: the
+// grouping's temporaries are dead by then.
+template <typename IT>
+__device__ __forceinline__ void ma_ordering(const Mem<IT> &m, const int32_t *grp, int32_t *nrep, int nsv,
+                            int kcap, Sh &sh) {
+  int32_t *acc = m.E, *key = m.F, *touched = m.H, *svl = m.G;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int contracted = 0;
@@ -331,44 +546,21 @@ __device__ void ma_ordering(const Mem &m, const int32_t *grp, int32_t *nrep, int
     for (int step = 0; step < nsv; ++step) {
       unsigned long long best = 0;
       for (int j = lane; j < nsv; j += 32) {
-        unsigned long long v = m.pk[j];
-        best = v > best ? v : best;
+        const int Y = svl[j];
+        if (!m.flag[Y]) {
+          const unsigned long long v = pack_key(key[Y], Y);
+          best = v > best ? v : best;
+        }
       }
       best = warp_max(best);
       const int X = (int)(~(unsigned)(best & 0xffffffffu));
-      const int kX = (int)(best >> 32);
       s = t;
       t = X;
-      cut = kX;
-      if (lane == 0) {
-        m.pk[pos[X]] = 0ull;
-        m.flag[X] = 1;
-      }
+      cut = (int)(best >> 32);
+      if (lane == 0) m.flag[X] = 1;
       __syncwarp();
       if (step == nsv - 1) break;  // the last super-vertex has no unadded neighbour
-      const int g = pos[X];
-      const int mb = m.C[g], me = m.C[g + 1];
-      if (me - mb == 1) {
-        const int i = m.D[mb];
-        for (int e = m.off[i] + lane; e < m.off[i + 1]; e += 32) {
-          int j = m.adj[e];
-          if (!m.alive[j]) continue;
-          int Y = grp[j];
-          if (Y == X || m.flag[Y]) continue;
-          if (atomicAdd(&acc[Y], 1) == 0) touched[atomicAdd(&sh.ntouched, 1)] = Y;
-        }
-      } else {
-        for (int q = mb + lane; q < me; q += 32) {
-          const int i = m.D[q];
-          for (int e = m.off[i]; e < m.off[i + 1]; ++e) {
-            int j = m.adj[e];
-            if (!m.alive[j]) continue;
-            int Y = grp[j];
-            if (Y == X || m.flag[Y]) continue;
-            if (atomicAdd(&acc[Y], 1) == 0) touched[atomicAdd(&sh.ntouched, 1)] = Y;
-          }
-        }
-      }
+      scan_super_vertex(m, grp, X, sh);
       __syncwarp();
       const int nt = sh.ntouched;
       for (int q = lane; q < nt; q += 32) {
@@ -382,7 +574,6 @@ __device__ void ma_ordering(const Mem &m, const int32_t *grp, int32_t *nrep, int
           contracted = 1;
         }
         key[Y] = nk;
-        m.pk[pos[Y]] = pack_key(nk, Y);
       }
       __syncwarp();
       if (lane == 0) sh.ntouched = 0;
@@ -399,7 +590,268 @@ __device__ void ma_ordering(const Mem &m, const int32_t *grp, int32_t *nrep, int
   __syncthreads();
 }
 
-__device__ void reset_ma_state(const Mem &m, int n) {
+// Bucket structure: clear levels 0..kcap, put every super-vertex (alive and,
+// when grp is given, grp[i] == i) in level 0.  Whole block.
+template <typename IT>
+__device__ __forceinline__ void buckets_init(const Mem<IT> &m, const int32_t *grp, int n, int kcap) {
+  const int W = m.W, S = m.S;
+  for (int q = threadIdx.x; q < (kcap + 1) * W; q += RB) m.bm[q] = 0u;
+  for (int q = threadIdx.x; q < (kcap + 1) * S; q += RB) m.bms[q] = 0u;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RB)
+    if (m.alive[i] && (grp == nullptr || grp[i] == i)) atomicOr(&m.bm[i >> 5], 1u << (i & 31));
+  __syncthreads();
+  for (int w = threadIdx.x; w < W; w += RB)
+    if (m.bm[w]) atomicOr(&m.bms[w >> 5], 1u << (w & 31));
+  __syncthreads();
+}
+
+// Warp 0: the not-yet-added super-vertex with the largest key, ties to the
+// smallest id = the lowest set bit of the highest non-empty bucket.  Returns
+// (level << 24) | id, or -1 if every bucket is empty (a broken invariant).
+template <typename IT>
+__device__ __forceinline__ int bucket_pick(const Mem<IT> &m, int kcap) {
+  const int lane = threadIdx.x & 31;
+  const int W = m.W, S = m.S;
+  volatile uint32_t *bm = m.bm, *bms = m.bms;
+  for (int L = kcap; L >= 0; --L) {
+    for (int s0 = 0; s0 < S; s0 += 32) {
+      const uint32_t sw = (s0 + lane < S) ? bms[L * S + s0 + lane] : 0u;
+      const unsigned b = __ballot_sync(FULL, sw != 0u);
+      if (b) {
+        const int fl = __ffs(b) - 1;
+        const uint32_t swv = __shfl_sync(FULL, sw, fl);
+        const int w = (s0 + fl) * 32 + __ffs(swv) - 1;
+        const uint32_t word = bm[L * W + w];
+        return (L << 24) | (w * 32 + __ffs(word) - 1);
+      }
+    }
+  }
+  return -1;
+}
+
+// Lane 0: take X out of bucket L.
+template <typename IT>
+__device__ __forceinline__ void bucket_remove_single(const Mem<IT> &m, int L, int X) {
+  const int w = X >> 5;
+  const uint32_t nw = m.bm[L * m.W + w] & ~(1u << (X & 31));
+  m.bm[L * m.W + w] = nw;
+  if (nw == 0u) m.bms[L * m.S + (w >> 5)] &= ~(1u << (w & 31));
+}
+
+// Concurrent moves by warp lanes: every lane clears first, then (after
+// __syncwarp) sets, so a summary bit is never cleared under a new member.
+template <typename IT>
+__device__ __forceinline__ void bucket_clear(const Mem<IT> &m, int L, int Y) {
+  const uint32_t bit = 1u << (Y & 31);
+  const uint32_t r = atomicAnd(&m.bm[L * m.W + (Y >> 5)], ~bit);
+  if ((r & ~bit) == 0u) atomicAnd(&m.bms[L * m.S + (Y >> 10)], ~(1u << ((Y >> 5) & 31)));
+}
+template <typename IT>
+__device__ __forceinline__ void bucket_set(const Mem<IT> &m, int L, int Y) {
+  atomicOr(&m.bm[L * m.W + (Y >> 5)], 1u << (Y & 31));
+  atomicOr(&m.bms[L * m.S + (Y >> 10)], 1u << ((Y >> 5) & 31));
+}
+
+// First contraction pass, on the item's own vertices (every super-vertex a
+// single vertex, every edge weight 1): the maximum-adjacency ordering with
+// keys capped at kcap, ties to the smallest id.  Each lane takes one
+// neighbour of the added vertex and moves it between buckets with
+// fire-and-forget atomics (a clear and a set touch different levels, and
+// bits of different neighbours never interfere); the entries whose key reaches kcap are marked (one bit per
+// adjacency entry) from a ballot, and the merges are applied afterwards by
+// the whole block.  Buckets of more than 64 words keep summary bits, set
+// eagerly and cleared lazily.  Returns whether anything merged; nrep
+// receives the merged sets labelled by their smallest id.
+template <typename IT>
+__device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<IT> &m, int32_t *nrep,
+                                              int n, int nsv, int kcap, int E, unsigned *err,
+                                              Sh &sh) {
+  const int W = m.W, S = m.S;
+  const bool summaries = W > 64;
+  for (int i = threadIdx.x; i < n; i += RB) m.kst[i] = m.alive[i] ? 0 : 255;
+  for (int q = threadIdx.x; q < (E + 31) / 32 + 1; q += RB) m.ebits[q] = 0u;
+  buckets_init(m, (const int32_t *)nullptr, n, kcap);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    volatile uint32_t *bm = m.bm, *bms = m.bms, *eb = m.ebits;
+    volatile uint8_t *kst = m.kst;
+    int contracted = 0;
+    int top = 0;
+    long long rows = 0;
+    const long long tp0 = P.prof ? clock64() : 0;
+    long long t_pick = 0, t_scan = 0;
+    const bool timing = P.prof != nullptr;
+    for (int step = 0; step < nsv; ++step) {
+      const long long c0 = timing ? clock64() : 0;
+      // pick: lowest set bit of the highest non-empty bucket
+      int X = -1;
+      for (;;) {
+        int cand = -1;
+        if (!summaries) {
+          const uint32_t w0 = lane < W ? bm[top * W + lane] : 0u;
+          const uint32_t w1 = lane + 32 < W ? bm[top * W + 32 + lane] : 0u;
+          const unsigned b0 = __ballot_sync(FULL, w0 != 0u);
+          const unsigned b1 = __ballot_sync(FULL, w1 != 0u);
+          if (b0 | b1) {
+            const int fl = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+            const uint32_t word = __shfl_sync(FULL, fl < 32 ? w0 : w1, fl & 31);
+            cand = fl * 32 + __ffs(word) - 1;
+          }
+        } else {
+          for (int s0 = 0; s0 < S && cand < 0; s0 += 32) {
+            const uint32_t sw = s0 + lane < S ? bms[top * S + s0 + lane] : 0u;
+            unsigned b = __ballot_sync(FULL, sw != 0u);
+            while (b) {
+              const int fl = __ffs(b) - 1;
+              const uint32_t swv = __shfl_sync(FULL, sw, fl);
+              const int widx = (s0 + fl) * 32 + lane;
+              const uint32_t wv = ((swv >> lane) & 1u) ? bm[top * W + widx] : 0u;
+              const unsigned bb = __ballot_sync(FULL, wv != 0u);
+              if (bb) {
+                const int ll = __ffs(bb) - 1;
+                const uint32_t word = __shfl_sync(FULL, wv, ll);
+                cand = ((s0 + fl) * 32 + ll) * 32 + __ffs(word) - 1;
+                break;
+              }
+              if (lane == 0) bms[top * S + s0 + fl] = 0u;  // every word it covers is empty
+              b &= b - 1;
+            }
+          }
+        }
+        if (cand >= 0) {
+          X = cand;
+          break;
+        }
+        if (top == 0) break;
+        --top;
+      }
+      if (X < 0) {
+        if (lane == 0) atomicOr(err, DERR_INTERNAL);
+        break;
+      }
+      if (lane == 0) {
+        atomicAnd(&m.bm[top * W + (X >> 5)], ~(1u << (X & 31)));
+        kst[X] = 255;
+      }
+      if (step == nsv - 1) break;
+      const long long c1 = timing ? clock64() : 0;
+      t_pick += c1 - c0;
+      const int b = m.off[X], e = m.off[X + 1];
+      rows += e - b;
+      int mx = 0;
+      for (int q0 = b; q0 < e; q0 += 32) {
+        const int q = q0 + lane;
+        bool sat = false;
+        if (q < e) {
+          const int j = m.adj[q];
+          const int ok = kst[j];
+          if (ok != 255) {
+            const int nk = ok + 1 < kcap ? ok + 1 : kcap;
+            sat = nk >= kcap;
+            if (nk != ok) {
+              atomicAnd(&m.bm[ok * W + (j >> 5)], ~(1u << (j & 31)));
+              atomicOr(&m.bm[nk * W + (j >> 5)], 1u << (j & 31));
+              if (summaries) atomicOr(&m.bms[nk * S + (j >> 10)], 1u << ((j >> 5) & 31));
+              kst[j] = (uint8_t)nk;
+              mx = nk > mx ? nk : mx;
+            }
+          }
+        }
+        const unsigned sm = __ballot_sync(FULL, sat);
+        if (sm && lane == 0) {
+          // entries q0 + l for the set lanes l: two words at most
+          const int w = q0 >> 5, sh5 = q0 & 31;
+          eb[w] |= sm << sh5;
+          if (sh5) eb[w + 1] |= sm >> (32 - sh5);
+        }
+        contracted |= sm != 0u;
+      }
+      const long long c2 = timing ? clock64() : 0;
+      t_scan += c2 - c1;
+      mx = __reduce_max_sync(FULL, mx);
+      top = mx > top ? mx : top;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      sh.contracted = contracted;
+      sh.dbg[0] = P.prof ? clock64() - tp0 : 0;
+      sh.dbg[1] = t_pick;
+      sh.dbg[2] = nsv;
+      sh.dbg[3] = t_scan;
+    }
+  }
+  __syncthreads();
+  const bool any = sh.contracted != 0;
+  if (any) components(m, n, sh, nrep, m.ebits);
+  return any;
+}
+
+// A later contraction pass (super-vertices with several members, integer
+// edge multiplicities) with the key buckets; merges every X-Y whose key
+// reaches kcap into nrep.  Same order and result as ma_ordering(kcap).
+// Needs group_members() and zeroed E (acc), F (key), flag.
+template <typename IT>
+__device__ __forceinline__ void ma_pass_bucketed(const Mem<IT> &m, const int32_t *grp, int32_t *nrep, int n,
+                                 int nsv, int kcap, unsigned *err, Sh &sh) {
+  int32_t *acc = m.E, *key = m.F, *touched = m.H;
+  buckets_init(m, grp, n, kcap);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int contracted = 0;
+    if (lane == 0) sh.ntouched = 0;
+    __syncwarp();
+    for (int step = 0; step < nsv; ++step) {
+      const int pk = bucket_pick(m, kcap);
+      if (pk < 0) {
+        if (lane == 0) atomicOr(err, DERR_INTERNAL);
+        break;
+      }
+      const int L = pk >> 24, X = pk & 0xffffff;
+      if (lane == 0) {
+        bucket_remove_single(m, L, X);
+        m.flag[X] = 1;
+      }
+      __syncwarp();
+      if (step == nsv - 1) break;
+      scan_super_vertex(m, grp, X, sh);
+      __syncwarp();
+      const int nt = sh.ntouched;
+      for (int q = lane; q < nt; q += 32) {
+        const int Y = touched[q];
+        const int a = acc[Y];
+        acc[Y] = 0;
+        const int ok = key[Y];
+        int nk = ok + a;
+        if (nk >= kcap) {
+          nk = kcap;
+          uf_union(nrep, X, Y);
+          contracted = 1;
+        }
+        if (nk != ok) {
+          bucket_clear(m, ok, Y);
+          key[Y] = nk;
+        } else {
+          touched[q] = -1 - Y;  // no move needed
+        }
+      }
+      __syncwarp();
+      for (int q = lane; q < nt; q += 32) {
+        const int Y = touched[q];
+        if (Y >= 0) bucket_set(m, key[Y], Y);
+      }
+      __syncwarp();
+      if (lane == 0) sh.ntouched = 0;
+      __syncwarp();
+    }
+    contracted = __any_sync(FULL, contracted);
+    if (lane == 0) sh.contracted = contracted;
+  }
+  __syncthreads();
+}
+
+template <typename IT>
+__device__ __forceinline__ void reset_ma_state(const Mem<IT> &m, int n) {
   for (int i = threadIdx.x; i < n; i += RB) {
     m.E[i] = 0;
     m.F[i] = 0;
@@ -409,93 +861,125 @@ __device__ void reset_ma_state(const Mem &m, int n) {
 }
 
 // ---- one work item ---------------------------------------------------------
-__device__ void process_item(const RefineParams &P, unsigned long long seq, const Item &it,
-                             char *smem, char *slab, Sh &sh) {
+template <typename IT, bool SM>
+__device__ __noinline__ int process_item(const RefineParams &P, unsigned long long seq,
+                                         const Item &it, char *slab, int64_t dbound, Sh &sh) {
+  char *base = SM ? wcc_dyn_smem : slab;
   const int n = it.n;
   const int64_t vbeg = it.vbeg;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   RunCounters *ctr = P.ctr;
+  Mem<IT> m = carve<IT>(base, n, dbound);
 
-  // upper bound on local edges: sum of global degrees of the members
-  long long dsum = 0;
+  // global row start and degree of every member
+  int64_t *gbeg = m.wide;
+  int32_t *pdeg = m.C, *cnt = m.D;
   for (int i = threadIdx.x; i < n; i += RB) {
-    int32_t v = P.pool[vbeg + i];
-    dsum += P.off[v + 1] - P.off[v];
+    const int32_t v = P.pool[vbeg + i];
+    m.gid[i] = v;
+    const int64_t b = P.off[v];
+    gbeg[i] = b;
+    pdeg[i] = (int32_t)(P.off[v + 1] - b);
+    cnt[i] = 0;
   }
-  dsum = block_sum_ll(dsum, sh);
-  const size_t need = ws_fixed_bytes(n) + 4 * (size_t)dsum + 64;
-  char *base;
-  size_t bytes;
-  if (need <= P.smem_bytes) {
-    base = smem;
-    bytes = P.smem_bytes;
-  } else {
-    base = slab;
-    bytes = P.slab_bytes;
-    if (need > bytes) {
-      if (threadIdx.x == 0) {
-        atomicOr(&ctr->error, DERR_CAPACITY);
-        atomicExch(&ctr->err_info, (unsigned)n);
-      }
-      return;
-    }
-  }
-  Mem m = carve(base, bytes, n);
-  for (int i = threadIdx.x; i < n; i += RB) m.gid[i] = P.pool[vbeg + i];
   __syncthreads();
+  const int D = block_scan_array(pdeg, n, sh);
+  if (threadIdx.x == 0) pdeg[n] = D;
+  __syncthreads();
+  prof_stamp(P, sh, 1);
 
-  // 1. extraction: count, scan, fill
-  for (int i = warp; i < n; i += RW) {
-    const int32_t v = m.gid[i];
-    const int64_t b = P.off[v], e = P.off[v + 1];
-    int c = 0;
-    for (int64_t q = b + lane; q < e; q += 32) {
-      unsigned long long s = P.slot[P.adj[q]];
-      c += (unsigned)(s >> 32) == (unsigned)seq;
+  // 1. extraction, flat over all D adjacency entries of the members so that
+  // every thread keeps independent loads in flight: entry f of row i keeps
+  // its neighbour u iff slot[u] names this item; tmp[f] = local id or ~0
+  IT *tmp = m.adj;
+  const IT NONE = (IT)~(IT)0;
+  {
+    // warp w owns entries [w*chunk, (w+1)*chunk); lane l takes every 32nd
+    // entry of it, four at a time, following its row with a cursor
+    const int chunk = (D + RW - 1) / RW;
+    const int f0 = warp * chunk, f1 = min(D, f0 + chunk);
+    int row = 0;
+    if (f0 + lane < f1) {
+      int lo = 0, hi = n;  // largest i with pdeg[i] <= f0 + lane
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pdeg[mid] <= f0 + lane) lo = mid; else hi = mid;
+      }
+      row = lo;
     }
-    c = warp_sum(c);
-    if (lane == 0) m.off[i] = c;
+    for (int fb = f0 + lane; fb < f1; fb += 128) {
+      int fs[4], rs[4];
+      int32_t us[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int f = fb + 32 * k;
+        fs[k] = f;
+        if (f < f1) {
+          while (pdeg[row + 1] <= f) ++row;
+          rs[k] = row;
+          us[k] = P.adj[gbeg[row] + (f - pdeg[row])];
+        }
+      }
+      unsigned long long sl[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sl[k] = fs[k] < f1 ? P.slot[us[k]] : 0ull;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (fs[k] >= f1) continue;
+        const bool hit = (unsigned)(sl[k] >> 32) == (unsigned)seq;
+        tmp[fs[k]] = hit ? (IT)(unsigned)(sl[k] & 0xffffffffu) : NONE;
+        if (hit) atomicAdd(&cnt[rs[k]], 1);
+      }
+    }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RB) m.off[i] = cnt[i];
   __syncthreads();
   const int E = block_scan_array(m.off, n, sh);
   if (threadIdx.x == 0) m.off[n] = E;
-  if (E > m.adj_cap) {
-    if (threadIdx.x == 0) atomicOr(&ctr->error, DERR_CAPACITY);
-    return;
-  }
-  for (int i = warp; i < n; i += RW) {
-    const int32_t v = m.gid[i];
-    const int64_t b = P.off[v], e = P.off[v + 1];
-    int w = m.off[i];
-    for (int64_t q0 = b; q0 < e; q0 += 32) {
-      int64_t q = q0 + lane;
-      bool hit = false;
-      int loc = 0;
-      if (q < e) {
-        unsigned long long s = P.slot[P.adj[q]];
-        hit = (unsigned)(s >> 32) == (unsigned)seq;
-        loc = (int)(unsigned)(s & 0xffffffffu);
+  // order-preserving compaction of tmp into the local adjacency, in chunks
+  // read fully into registers before any write (destinations never pass the
+  // chunk's own sources)
+  {
+    constexpr int CI = 4;
+    int carry = 0;
+    for (int c0 = 0; c0 < D; c0 += RB * CI) {
+      IT v[CI];
+      int k = 0;
+#pragma unroll
+      for (int q = 0; q < CI; ++q) {
+        const int f = c0 + threadIdx.x * CI + q;
+        v[q] = f < D ? tmp[f] : NONE;
+        k += v[q] != NONE;
       }
-      unsigned mask = __ballot_sync(FULL, hit);
-      if (hit) m.adj[w + __popc(mask & lanemask_lt())] = loc;
-      w += __popc(mask);
+      int tot;
+      int ex = block_exclusive_scan<RB>(k, &tot, sh.scan);
+      int w = carry + ex;
+#pragma unroll
+      for (int q = 0; q < CI; ++q)
+        if (v[q] != NONE) m.adj[w++] = v[q];
+      carry += tot;
+      __syncthreads();
     }
   }
   for (int i = threadIdx.x; i < n; i += RB) m.alive[i] = 1;
   __syncthreads();
   if (threadIdx.x == 0) {
     add_ll(&ctr->items, 1ll);
-    add_ll(&ctr->alg_bytes, (long long)(4 * n + 16 * n + 12 * dsum));
+    add_ll(&ctr->alg_bytes, (long long)(4 * n + 16 * n + 12 * (long long)D));
+    sh.pf_E = E;
   }
+  prof_stamp(P, sh, 2);
 
   // 2. input cluster: CCR (Algorithm 1)
   if (it.flags & ITEM_TOP) {
-    int nc = components(m, n, sh);
+    int nc = components_af(m, n, m.B, m.H, sh);
     if (nc != 1) {
       emit_children(P, m, m.B, n, vbeg, sh);
-      return;
+      return OUT_CCR_SPLIT;
     }
   }
+  prof_stamp(P, sh, 3);
 
   // 3. peel (round-synchronous, T recomputed from the alive count)
   int32_t *deg = m.A;
@@ -520,39 +1004,68 @@ __device__ void process_item(const RefineParams &P, unsigned long long seq, cons
     __syncthreads();
     nalive -= rem;
   }
-  if (threadIdx.x == 0 && nalive < n) add_ll(&ctr->peeled, (long long)(n - nalive));
-  if (nalive < P.min_size) return;
+  if (threadIdx.x == 0) {
+    if (nalive < n) add_ll(&ctr->peeled, (long long)(n - nalive));
+    sh.pf_nalive = nalive;
+  }
+  prof_stamp(P, sh, 4);
+  if (nalive < P.min_size) return OUT_DROPPED;
 
-  // 4. connectivity of what is left
-  {
-    int nc = components(m, n, sh);
+  // 4. connectivity of what is left (an item arrives connected: input
+  // clusters passed CCR above, children are components or sides of a
+  // minimum cut, which are connected; only a peel can disconnect it)
+  if (nalive < n) {
+    int nc = components_af(m, n, m.B, m.H, sh);
     if (nc > 1) {
       emit_children(P, m, m.B, n, vbeg, sh);
-      return;
+      return OUT_CC_SPLIT;
     }
   }
+  prof_stamp(P, sh, 5);
 
   // 5. contraction with k = T+1
   const int64_t T = threshold_of(P.rule_kind, P.rule_num, P.rule_den, nalive);
   const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
   int32_t *rep = m.A, *nrep = m.B;
-  for (int i = threadIdx.x; i < n; i += RB) rep[i] = m.alive[i] ? i : -1;
-  __syncthreads();
-  int nsv;
-  for (;;) {
-    nsv = group_members(m, rep, n, sh);
-    if (nsv <= 1) break;
-    reset_ma_state(m, n);
-    for (int i = threadIdx.x; i < n; i += RB) nrep[i] = i;
-    __syncthreads();
-    if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
-    ma_ordering(m, rep, nrep, nsv, kcap, sh);
-    if (!sh.contracted) break;
-    for (int i = threadIdx.x; i < n; i += RB)
-      if (m.alive[i]) rep[i] = uf_find(nrep, rep[i]);
-    __syncthreads();
+  int nsv = 1, passes = 0;
+  {
+    nsv = nalive;
+    bool more = true;
+    const bool bucketed = kcap < KB_LEVELS && n < (1 << 24);  // pick packs the id in 24 bits
+    if (bucketed) {
+      if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
+      ++passes;
+      const bool any = ma_pass_first(P, m, nrep, n, nalive, kcap, E, &ctr->error, sh);
+      for (int i = threadIdx.x; i < n; i += RB) rep[i] = m.alive[i] ? (any ? nrep[i] : i) : -1;
+      __syncthreads();
+      more = any;
+    } else {
+      for (int i = threadIdx.x; i < n; i += RB) rep[i] = m.alive[i] ? i : -1;
+      __syncthreads();
+    }
+    while (more) {
+      nsv = group_members(m, rep, n, sh);
+      if (nsv <= 1) break;
+      reset_ma_state(m, n);
+      for (int i = threadIdx.x; i < n; i += RB) nrep[i] = i;
+      __syncthreads();
+      if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
+      ++passes;
+      if (bucketed)
+        ma_pass_bucketed(m, rep, nrep, n, nsv, kcap, &ctr->error, sh);
+      else
+        ma_ordering(m, rep, nrep, nsv, kcap, sh);
+      if (!sh.contracted) break;
+      for (int i = threadIdx.x; i < n; i += RB)
+        if (m.alive[i]) rep[i] = uf_find(nrep, rep[i]);
+      __syncthreads();
+    }
   }
-
+  if (threadIdx.x == 0) {
+    sh.pf_passes = passes;
+    sh.pf_nsv = nsv;
+  }
+  prof_stamp(P, sh, 6);
   if (nsv <= 1) {
     // accept (Algorithm 3: save V_c); output id resolved after the run
     if (threadIdx.x == 0) sh.i0 = n;
@@ -565,42 +1078,74 @@ __device__ void process_item(const RefineParams &P, unsigned long long seq, cons
       if (m.alive[i]) P.label_min[m.gid[i]] = minv;
     if (threadIdx.x == 0) add_ll(&ctr->accepted, 1ll);
     __syncthreads();
-    return;
+    return OUT_ACCEPT;
   }
 
   // 6. canonical Stoer-Wagner on the contracted graph; grp = A (starts as rep)
-  int32_t *grp = m.A;
-  int best = 0x7fffffff;
-  while (nsv > 1) {
-    group_members(m, grp, n, sh);
-    reset_ma_state(m, n);
-    if (threadIdx.x == 0) add_ll(&ctr->sw_phases, 1ll);
-    ma_ordering(m, grp, nullptr, nsv, 0, sh);
-    const int s = sh.sw_s, t = sh.sw_t, cut = sh.sw_cut;
-    if (cut < best) {
-      best = cut;
-      for (int i = threadIdx.x; i < n; i += RB) m.side[i] = m.alive[i] && grp[i] == t;
+  {
+    int32_t *grp = m.A;
+    int best = 0x7fffffff;
+    while (nsv > 1) {
+      group_members(m, grp, n, sh);
+      reset_ma_state(m, n);
+      if (threadIdx.x == 0) add_ll(&ctr->sw_phases, 1ll);
+      ma_ordering(m, grp, (int32_t *)nullptr, nsv, 0, sh);
+      const int s = sh.sw_s, t = sh.sw_t, cut = sh.sw_cut;
+      if (cut < best) {
+        best = cut;
+        for (int i = threadIdx.x; i < n; i += RB) m.side[i] = m.alive[i] && grp[i] == t;
+      }
+      __syncthreads();
+      const int lo = s < t ? s : t, hi = s < t ? t : s;
+      for (int i = threadIdx.x; i < n; i += RB)
+        if (m.alive[i] && grp[i] == hi) grp[i] = lo;
+      __syncthreads();
+      --nsv;
     }
-    __syncthreads();
-    const int lo = s < t ? s : t, hi = s < t ? t : s;
-    for (int i = threadIdx.x; i < n; i += RB)
-      if (m.alive[i] && grp[i] == hi) grp[i] = lo;
-    __syncthreads();
-    --nsv;
-  }
-  if (best > T) {
-    if (threadIdx.x == 0) atomicOr(&ctr->error, DERR_INTERNAL);
-    return;
+    prof_stamp(P, sh, 7);
+    if (best > T) {
+      if (threadIdx.x == 0) atomicOr(&ctr->error, DERR_INTERNAL);
+      return OUT_ERROR;
+    }
   }
   if (threadIdx.x == 0) add_ll(&ctr->splits, 1ll);
   for (int i = threadIdx.x; i < n; i += RB) m.B[i] = m.alive[i] ? (m.side[i] ? 1 : 0) : -1;
   __syncthreads();
   emit_children(P, m, m.B, n, vbeg, sh);
+  return OUT_CUT_SPLIT;
+}
+
+// Chooses the local id width and the memory (shared or the CTA's slab) for
+// an item, then processes it.
+__device__ int run_item(const RefineParams &P, unsigned long long seq, const Item &it, char *slab,
+                        Sh &sh) {
+  const int n = it.n;
+  long long dsum = 0;
+  for (int i = threadIdx.x; i < n; i += RB) {
+    const int32_t v = P.pool[it.vbeg + i];
+    dsum += P.off[v + 1] - P.off[v];
+  }
+  dsum = block_sum_ll(dsum, sh);
+  const bool narrow = n < 65535;
+  const size_t need = narrow ? ws_bytes<uint16_t>(n, dsum) : ws_bytes<int32_t>(n, dsum);
+  const bool in_smem = need <= P.smem_bytes;
+  if (!in_smem && (need > P.slab_bytes || dsum >= (1ll << 31))) {
+    if (threadIdx.x == 0) {
+      atomicOr(&P.ctr->error, DERR_CAPACITY);
+      atomicExch(&P.ctr->err_info, (unsigned)n);
+    }
+    return OUT_ERROR;
+  }
+  if (threadIdx.x == 0) sh.used_slab = !in_smem;
+  if (in_smem)
+    return narrow ? process_item<uint16_t, true>(P, seq, it, slab, dsum, sh)
+                  : process_item<int32_t, true>(P, seq, it, slab, dsum, sh);
+  return narrow ? process_item<uint16_t, false>(P, seq, it, slab, dsum, sh)
+                : process_item<int32_t, false>(P, seq, it, slab, dsum, sh);
 }
 
 // ---- the persistent kernel ---------------------------------------------------
 __global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
-  extern __shared__ __align__(16) char smem[];
   __shared__ Sh sh;
   char *slab = P.slab + (size_t)blockIdx.x * P.slab_bytes;
   RunCounters *ctr = P.ctr;
@@ -642,8 +1187,41 @@ __global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
     __syncthreads();
     if (!sh.go) break;
     const Item it = sh.item;
-    process_item(P, sh.seq, it, smem, slab, sh);
+    if (P.prof && threadIdx.x == 0) {
+      const long long t = clock64();
+      for (int k = 0; k < 9; ++k) sh.ts[k] = t;
+      sh.used_slab = 0;
+      sh.pf_E = sh.pf_nalive = sh.pf_passes = sh.pf_nsv = -1;
+      for (int k = 0; k < 4; ++k) sh.dbg[k] = 0;
+    }
     __syncthreads();
+    const int outcome = run_item(P, sh.seq, it, slab, sh);
+    __syncthreads();
+    if (P.prof && threadIdx.x == 0) {
+      // fill skipped stamps forward, then record
+      sh.ts[8] = clock64();
+      for (int k = 1; k < 8; ++k)
+        if (sh.ts[k] < sh.ts[k - 1]) sh.ts[k] = sh.ts[k - 1];
+      const unsigned r = atomicAdd(P.prof_count, 1u);
+      if (r < P.prof_cap) {
+        ItemProf *q = &P.prof[r];
+        q->seq = (unsigned)sh.seq;
+        q->n = it.n;
+        q->E = sh.pf_E;
+        q->nalive = sh.pf_nalive;
+        q->passes = sh.pf_passes;
+        q->nsv = sh.pf_nsv;
+        q->outcome = outcome;
+        unsigned smid;
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        q->smid = (int)smid;
+        q->slab = sh.used_slab;
+        q->top = (int)(it.flags & ITEM_TOP);
+        for (int k = 0; k < 8; ++k) q->dt[k] = (unsigned)(sh.ts[k + 1] - sh.ts[k]);
+        q->t_begin = sh.ts[0];
+        for (int k = 0; k < 4; ++k) q->dbg[k] = sh.dbg[k];
+      }
+    }
     if (threadIdx.x == 0) {
       __threadfence();
       add_ll(&ctr->pending, -1ll);
@@ -654,38 +1232,52 @@ __global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
 
 }  // namespace
 
-size_t item_workspace_bytes(int64_t n, int64_t e) { return ws_fixed_bytes(n) + 4 * (size_t)e + 64; }
+size_t item_workspace_bytes(int64_t n, int64_t d) {
+  return n < 65535 ? ws_bytes<uint16_t>(n, d) : ws_bytes<int32_t>(n, d);
+}
 
 int refine_block_threads() { return RB; }
 
-size_t refine_smem_bytes() { return SMEM_BYTES; }
+// Largest dynamic shared memory a refinement CTA can opt into on this
+// device: the per-block opt-in limit minus the kernel's static shared memory.
+size_t refine_smem_max_bytes(int device) {
+  int optin = 0;
+  WCC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  cudaFuncAttributes fa;
+  WCC_CUDA(cudaFuncGetAttributes(&fa, k_refine));
+  size_t mx = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  mx &= ~(size_t)1023;
+  return mx < SMEM_MAX_BYTES ? mx : SMEM_MAX_BYTES;
+}
 
-int refine_max_ctas(int device) {
-  static int cached[64] = {0};
-  if (device >= 0 && device < 64 && cached[device]) return cached[device];
+static void set_smem_attr(int device) {
   WCC_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SMEM_BYTES));
+                                (int)refine_smem_max_bytes(device)));
+}
+
+int refine_max_ctas(int device, size_t smem_bytes) {
+  set_smem_attr(device);
   int per_sm = 0;
-  WCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, RB, SMEM_BYTES));
+  WCC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine, RB, smem_bytes));
   int sms = 0;
   WCC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   int r = per_sm * sms;
   if (r < 1) fail(WCC_ERR_CUDA, "refinement kernel cannot be resident on this device");
-  if (device >= 0 && device < 64) cached[device] = r;
   return r;
 }
 
 void launch_refine(const RefineParams &p, int grid, bool cooperative, cudaStream_t s) {
-  WCC_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SMEM_BYTES));
+  int device = 0;
+  WCC_CUDA(cudaGetDevice(&device));
+  set_smem_attr(device);
   RefineParams pc = p;
   if (cooperative) {
     void *args[] = {&pc};
     WCC_CUDA(cudaLaunchCooperativeKernel((const void *)k_refine, dim3(grid), dim3(RB), args,
-                                         SMEM_BYTES, s));
+                                         p.smem_bytes, s));
     note_launch();
   } else {
-    k_refine<<<grid, RB, SMEM_BYTES, s>>>(pc); note_launch();
+    k_refine<<<grid, RB, p.smem_bytes, s>>>(pc); note_launch();
     WCC_CUDA(cudaGetLastError());
   }
 }
