@@ -145,6 +145,35 @@ int wcc_run(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshol
 /* Release a graph (NULL is ignored). */
 void wcc_destroy_graph(wcc_graph *g);
 
+/* Build a CSR without allocating any memory.  The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory, for
+ * example code running under an allocator that owns the whole device, a
+ * host framework that forbids allocation after start-up, or a caller that
+ * must not add allocations to a carefully sized memory budget.  It computes
+ * the same CSR as wcc_create_graph_from_edges + wcc_graph_export_csr (both
+ * directions, self-loops and repeated edges dropped, rows sorted) but writes
+ * it straight into the caller's device buffers.
+ *   src[m], dst[m]  device int32 edge endpoints in [0, n).
+ *   row_off[n+1]    device int64 output; cols: device int32 output with room
+ *                   for 2*m entries (the first *nnz are written).
+ *   nnz             host int64 output: number of directed entries.
+ *   stream          cudaStream_t the work is ordered on (NULL = legacy
+ *                   default stream); the call returns after it finishes.
+ * Limits: m <= 131072 (2^17) and n <= 4194304 (2^22); larger inputs return
+ * WCC_ERR_INVALID with a message naming the limit, as does an endpoint
+ * outside [0, n).
+ * Its working memory is one fixed array of about 6.5 MB in the library's
+ * static device memory, present on every GPU that loads the library until
+ * the process exits; the call itself performs no device allocation.  The
+ * array is shared by all calls and keeps the last call's contents (each call
+ * clears what it needs), so calls that may overlap on the GPU -- different
+ * streams, or several host threads -- race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream
+ * capture. */
+int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                           int64_t *row_off, int32_t *cols, int64_t *nnz, void *stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (instrumentation: lets a caller count the kernels of a timed region). */
 int64_t wcc_kernel_launches(void);

@@ -13,7 +13,8 @@ import numpy as np
 
 from . import _binding
 from ._binding import (WCC_MODE_BATCHED, WCC_MODE_PLAIN, WCC_RULE_LINEAR,  # noqa: F401
-                       WCC_RULE_LOG2, WCC_RULE_LOG10, WCC_RULE_SQRT, WccError, wcc_create_graph,
+                       WCC_RULE_LOG2, WCC_RULE_LOG10, WCC_RULE_SQRT, WccError,
+                       wcc_build_csr_no_alloc, wcc_create_graph,
                        wcc_create_graph_from_edges, wcc_destroy_graph, wcc_graph_export_csr,
                        wcc_graph_nnz, wcc_graph_num_vertices, wcc_kernel_launches,
                        wcc_last_error, wcc_run,
@@ -127,6 +128,6 @@ class WccGraph:
 
 __all__ = ["WccGraph", "WccError", "rule_struct", "wcc_create_graph",
            "wcc_create_graph_from_edges", "wcc_run", "wcc_destroy_graph", "wcc_last_error",
-           "wcc_graph_num_vertices", "wcc_graph_nnz", "wcc_kernel_launches", "wcc_graph_export_csr", "wcc_stats",
+           "wcc_graph_num_vertices", "wcc_graph_nnz", "wcc_kernel_launches", "wcc_build_csr_no_alloc", "wcc_graph_export_csr", "wcc_stats",
            "wcc_threshold_rule", "WCC_MODE_BATCHED", "WCC_MODE_PLAIN"]
 _ = ctypes

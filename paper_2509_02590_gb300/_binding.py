@@ -74,6 +74,8 @@ def _load():
     L.wcc_run.restype = c_int
     L.wcc_destroy_graph.argtypes = [vp]
     L.wcc_destroy_graph.restype = None
+    L.wcc_build_csr_no_alloc.argtypes = [vp, vp, i64, i64, vp, vp, ctypes.POINTER(i64), vp]
+    L.wcc_build_csr_no_alloc.restype = c_int
     L.wcc_kernel_launches.argtypes = []
     L.wcc_kernel_launches.restype = i64
     L.wcc_last_error.argtypes = []
@@ -82,6 +84,14 @@ def _load():
 
 
 lib = _load()
+
+
+def wcc_build_csr_no_alloc(src: int, dst: int, m: int, n: int, row_off: int, cols: int,
+                           stream: int) -> int:
+    """Device-buffer CSR build that allocates nothing; returns nnz."""
+    nnz = ctypes.c_int64(0)
+    _check(lib.wcc_build_csr_no_alloc(src, dst, m, n, row_off, cols, ctypes.byref(nnz), stream))
+    return int(nnz.value)
 
 
 def wcc_kernel_launches() -> int:

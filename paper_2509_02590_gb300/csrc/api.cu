@@ -691,6 +691,85 @@ Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int6
   return g.release();
 }
 
+// ---------------------------------------------------------------- CSR build without allocation
+// Scratch of wcc_build_csr_no_alloc: one array in the module's static device
+// memory, so a caller that must not allocate device memory can still build a
+// CSR.  Every GPU that loads this library holds it until the process exits.
+// Layout (256-byte aligned pieces): two 64-bit key buffers and two 32-bit
+// flag/position buffers of 2*NOALLOC_MAX_EDGES (+1) entries, the sort/scan
+// temporaries, and a small result word.
+constexpr int64_t NOALLOC_MAX_EDGES = 1 << 17;
+constexpr int64_t NOALLOC_MAX_VERTICES = 1 << 22;
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)6656 * 1024;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on `dev`, looked up once per device
+// (with that device current) and cached.
+void *noalloc_scratch(int dev) {
+  static std::mutex mu;
+  static void *addr[64] = {nullptr};
+  if (dev < 0 || dev >= 64) fail(WCC_ERR_CUDA, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      (void)cudaGetLastError();
+      fail(WCC_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") +
+                             cudaGetErrorString(e));
+    }
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+void build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                        int64_t *row_off, int32_t *cols, int64_t *nnz_out, cudaStream_t s) {
+  if (m < 0 || m > NOALLOC_MAX_EDGES)
+    fail(WCC_ERR_INVALID, "wcc_build_csr_no_alloc: m must be in [0, " +
+                              std::to_string(NOALLOC_MAX_EDGES) + "], got " + std::to_string(m));
+  if (n < 0 || n > NOALLOC_MAX_VERTICES)
+    fail(WCC_ERR_INVALID, "wcc_build_csr_no_alloc: n must be in [0, " +
+                              std::to_string(NOALLOC_MAX_VERTICES) + "], got " +
+                              std::to_string(n));
+  if (row_off == nullptr || nnz_out == nullptr || (m > 0 && (src == nullptr || dst == nullptr || cols == nullptr)))
+    fail(WCC_ERR_INVALID, "wcc_build_csr_no_alloc: NULL buffer");
+  const int dev = current_device();
+  char *base = static_cast<char *>(noalloc_scratch(dev));
+  const int64_t n2 = 2 * m;
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t cap2 = (size_t)(2 * NOALLOC_MAX_EDGES);
+  size_t o = 0;
+  uint64_t *k1 = reinterpret_cast<uint64_t *>(base + o); o += al(8 * cap2);
+  uint64_t *k2 = reinterpret_cast<uint64_t *>(base + o); o += al(8 * cap2);
+  uint32_t *keep = reinterpret_cast<uint32_t *>(base + o); o += al(4 * (cap2 + 1));
+  uint32_t *pos = reinterpret_cast<uint32_t *>(base + o); o += al(4 * (cap2 + 1));
+  unsigned *err = reinterpret_cast<unsigned *>(base + o); o += al(16);
+  void *temp = base + o;
+  o += al(std::max(radix_temp_bytes((int64_t)cap2), scan_temp_bytes(NOALLOC_MAX_VERTICES + 1)));
+  if (o > NOALLOC_SCRATCH_BYTES) fail(WCC_ERR_INTERNAL, "no-alloc scratch layout exceeds its array");
+  // the degree counts accumulate in row_off, and the error word must start clear
+  WCC_CUDA(cudaMemsetAsync(row_off, 0, 8 * (size_t)(n + 1), s));
+  WCC_CUDA(cudaMemsetAsync(err, 0, 16, s));
+  int64_t nnz = 0;
+  if (m > 0) {
+    const int b = std::max(1, bitlen_u64(n > 0 ? (uint64_t)(n - 1) : 0));
+    k_edge_keys<<<blocks_for(m), TB, 0, s>>>(src, dst, m, n, b, k1, err); note_launch();
+    WCC_CUDA(cudaGetLastError());
+    if (read_back(err, s)) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
+    uint64_t *sorted = radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, s) ? k2 : k1;
+    k_unique_flags<<<blocks_for(n2), TB, 0, s>>>(sorted, n2, keep, ~0ull); note_launch();
+    exclusive_scan_u32(keep, pos, n2, pos + n2, temp, s);
+    k_compact_edges<<<blocks_for(n2), TB, 0, s>>>(sorted, keep, pos, n2, b, cols, row_off);
+    note_launch();
+    exclusive_scan_i64(row_off, row_off, n + 1, nullptr, temp, s);
+    WCC_CUDA(cudaGetLastError());
+    nnz = (int64_t)read_back(pos + n2, s);
+  }
+  WCC_CUDA(cudaStreamSynchronize(s));
+  *nnz_out = nnz;
+}
+
 template <typename F>
 int guarded(F &&f) {
   try {
@@ -781,6 +860,13 @@ void wcc_destroy_graph(wcc_graph *g) {
     delete dg;
   }
   delete g;
+}
+
+int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                           int64_t *row_off, int32_t *cols, int64_t *nnz, void *stream) {
+  return guarded([&] {
+    build_csr_no_alloc(src, dst, m, n, row_off, cols, nnz, (cudaStream_t)stream);
+  });
 }
 
 int64_t wcc_kernel_launches(void) { return launches_so_far(); }
