@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -20,19 +21,74 @@ static std::atomic<int64_t> g_launches{0};
 void note_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+// Process-wide cache of device blocks, per device and power-of-two size
+// class.  Every API call ends with a stream synchronisation, so a block that
+// a finished call released can be handed to the next call at once; a graph
+// created and destroyed per request then costs no cudaMalloc / cudaFree (and
+// no device-wide synchronisation of cudaFree) after the first one.  When an
+// allocation fails, the cached blocks of that device are returned to the
+// driver and the allocation retried once.
+namespace {
+struct BlockCache {
+  std::mutex mu;
+  std::unordered_map<uint64_t, std::vector<void *>> free_blocks;  // (device << 8 | class)
+};
+BlockCache &block_cache() {
+  static BlockCache *c = new BlockCache();  // never destroyed: blocks live until exit
+  return *c;
+}
+int size_class(size_t b) {
+  int k = 8;  // 256 bytes
+  while (((size_t)1 << k) < b) ++k;
+  return k;
+}
+void trim_cache(int dev) {
+  BlockCache &c = block_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  for (auto &kv : c.free_blocks) {
+    if ((int)(kv.first >> 8) != dev) continue;
+    for (void *q : kv.second) cudaFree(q);
+    kv.second.clear();
+  }
+}
+}  // namespace
+
 DevBuf::~DevBuf() { release(); }
 
 void DevBuf::release() {
-  if (p) cudaFree(p);
+  if (p) {
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.free_blocks[((uint64_t)dev << 8) | (uint64_t)size_class(bytes)].push_back(p);
+  }
   p = nullptr;
   bytes = 0;
+  dev = -1;
 }
 
 void *DevBuf::ensure(size_t b) {
   if (b <= bytes && p) return p;
   release();
-  size_t want = b < 256 ? 256 : b;
+  const int k = size_class(b);
+  const size_t want = (size_t)1 << k;
+  WCC_CUDA(cudaGetDevice(&dev));
+  {
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.free_blocks.find(((uint64_t)dev << 8) | (uint64_t)k);
+    if (it != c.free_blocks.end() && !it->second.empty()) {
+      p = it->second.back();
+      it->second.pop_back();
+      bytes = want;
+      return p;
+    }
+  }
   cudaError_t e = cudaMalloc(&p, want);
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    trim_cache(dev);
+    e = cudaMalloc(&p, want);
+  }
   if (e != cudaSuccess) {
     p = nullptr;
     (void)cudaGetLastError();
@@ -135,6 +191,17 @@ __global__ void k_compact_edges(const uint64_t *__restrict__ keys, const uint32_
 }
 
 // ---------------------------------------------------------------- membership
+struct SeedInfo {
+  unsigned long long max_n;     // largest kept cluster
+  unsigned long long max_dsum;  // largest degree sum of a kept cluster
+  long long clusters;           // K: distinct labels
+  long long skip;               // unclustered vertices (they sort first)
+  unsigned err;                 // DERR_* bits
+  unsigned maxkey;              // largest label + 1
+  unsigned kept;                // clusters with >= min_size members
+  unsigned pad;
+};
+
 __global__ void k_make_keys(const int32_t *__restrict__ lab, int64_t n, uint32_t *keys,
                             uint32_t *vals, unsigned *maxkey, unsigned *err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -156,13 +223,22 @@ __global__ void k_heads(const uint32_t *__restrict__ sk, int64_t n, uint32_t *he
   head[i] = (sk[i] != 0 && (i == 0 || sk[i - 1] != sk[i])) ? 1u : 0u;
 }
 
+// cstart[c] = first sorted position of cluster c, cstart[K] = n; also
+// records K and the number of unclustered vertices (they sort first).
 __global__ void k_starts(const uint32_t *__restrict__ head, const uint32_t *__restrict__ hidx,
-                         int64_t n, int64_t *cstart) {
+                         int64_t n, int64_t *cstart, SeedInfo *info) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && head[i]) cstart[hidx[i]] = i;
+  const int64_t K = hidx[n];
+  if (i < n && head[i]) {
+    cstart[hidx[i]] = i;
+    if (hidx[i] == 0) info->skip = i;
+  }
+  if (i == 0) {
+    cstart[K] = n;
+    info->clusters = K;
+    if (K == 0) info->skip = n;
+  }
 }
-
-__global__ void k_set_i64(int64_t *p, int64_t v) { *p = v; }
 
 // degree of each vertex in sorted order (for the per-cluster degree sums)
 __global__ void k_sorted_deg(const uint32_t *__restrict__ sv, const int64_t *__restrict__ off,
@@ -173,19 +249,15 @@ __global__ void k_sorted_deg(const uint32_t *__restrict__ sv, const int64_t *__r
   dg[i] = off[v + 1] - off[v];
 }
 
-struct SeedInfo {
-  unsigned long long max_n;     // largest kept cluster
-  unsigned long long max_dsum;  // largest degree sum of a kept cluster
-  unsigned err;                 // DERR_* bits
-  unsigned maxkey;              // largest label + 1
-  unsigned kept;                // clusters with >= min_size members
-  unsigned pad;
-};
 
-__global__ void k_keep(const int64_t *__restrict__ cstart, int64_t K, int min_size,
-                       uint32_t *keep, const int64_t *__restrict__ pdeg, SeedInfo *info) {
+
+__global__ void k_keep(const int64_t *__restrict__ cstart, const uint32_t *__restrict__ Kp,
+                       int64_t cap, int min_size, uint32_t *keep,
+                       const int64_t *__restrict__ pdeg, SeedInfo *info) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t K = *Kp;
   unsigned long long sz = 0, ds = 0;
+  if (c < cap && c >= K) keep[c] = 0u;
   if (c < K) {
     sz = (unsigned long long)(cstart[c + 1] - cstart[c]);
     bool k = (int64_t)sz >= min_size;
@@ -432,37 +504,28 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
   uint32_t *hidx = static_cast<uint32_t *>(ws[W_HIDX].ensure(4 * (n + 1)));
   k_heads<<<blocks_for(n), TB, 0, s>>>(sk, n, head); note_launch();
   WCC_CUDA(cudaGetLastError());
-  // hidx[n] receives the number of distinct labels
+  // hidx[n] receives the number of distinct labels K; arrays indexed by
+  // cluster are sized by n so that K need not be read back here
   exclusive_scan_u32(head, hidx, n, hidx + n, temp, s);
-  const int64_t K = (int64_t)read_back(hidx + n, s);
-  // unclustered vertices (key 0) sort first
-  int64_t skip = 0;
-  int64_t *cstart = static_cast<int64_t *>(ws[W_CSTART].ensure(8 * (K + 1)));
-  if (K > 0) {
-    k_starts<<<blocks_for(n), TB, 0, s>>>(head, hidx, n, cstart); note_launch();
-    k_set_i64<<<1, 1, 0, s>>>(cstart + K, n); note_launch();
-    WCC_CUDA(cudaGetLastError());
-    skip = read_back(cstart, s);
-  } else {
-    skip = n;
-  }
+  int64_t *cstart = static_cast<int64_t *>(ws[W_CSTART].ensure(8 * (n + 1)));
+  k_starts<<<blocks_for(n), TB, 0, s>>>(head, hidx, n, cstart, info); note_launch();
 
   // per-cluster degree sums (prefix sums of degrees in sorted order)
   int64_t *dg = static_cast<int64_t *>(ws[W_DG].ensure(8 * (n + 1)));
   int64_t *pdeg = static_cast<int64_t *>(ws[W_PDEG].ensure(8 * (n + 1)));
-  uint32_t *keep = static_cast<uint32_t *>(ws[W_KEEP].ensure(4 * (K + 1)));
-  uint32_t *qidx = static_cast<uint32_t *>(ws[W_QIDX].ensure(4 * (K + 1)));
-  int64_t nkept = 0;
-  SeedInfo hi{};
-  if (K > 0) {
-    k_sorted_deg<<<blocks_for(n), TB, 0, s>>>(sv, g->off.as<int64_t>(), n, dg); note_launch();
-    WCC_CUDA(cudaMemsetAsync(dg + n, 0, 8, s));
-    exclusive_scan_i64(dg, pdeg, n + 1, nullptr, temp, s);
-    k_keep<<<blocks_for(K), TB, 0, s>>>(cstart, K, min_size, keep, pdeg, info); note_launch();
-    exclusive_scan_u32(keep, qidx, K, &info->kept, temp, s);
-    WCC_CUDA(cudaGetLastError());
-    hi = read_back(info, s);
-    nkept = (int64_t)hi.kept;
+  uint32_t *keep = static_cast<uint32_t *>(ws[W_KEEP].ensure(4 * (n + 1)));
+  uint32_t *qidx = static_cast<uint32_t *>(ws[W_QIDX].ensure(4 * (n + 1)));
+  k_sorted_deg<<<blocks_for(n), TB, 0, s>>>(sv, g->off.as<int64_t>(), n, dg); note_launch();
+  WCC_CUDA(cudaMemsetAsync(dg + n, 0, 8, s));
+  exclusive_scan_i64(dg, pdeg, n + 1, nullptr, temp, s);
+  k_keep<<<blocks_for(n), TB, 0, s>>>(cstart, hidx + n, n, min_size, keep, pdeg, info); note_launch();
+  exclusive_scan_u32(keep, qidx, n, &info->kept, temp, s);
+  WCC_CUDA(cudaGetLastError());
+  SeedInfo hi = read_back(info, s);
+  const int64_t K = hi.clusters;
+  const int64_t skip = hi.skip;
+  const int64_t nkept = (int64_t)hi.kept;
+  {
     if (nkept > 1) {
       // queue order: largest input clusters first (qidx = rank by size)
       uint32_t *ok1 = static_cast<uint32_t *>(ws[W_OK1].ensure(4 * K));
@@ -642,7 +705,7 @@ Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int6
   std::unique_ptr<Graph> g(new Graph());
   g->device = current_device();
   g->n = n;
-  DevBuf bsrc, bdst, bk, bk2, btemp, bkeep, bpos, bdeg;
+  DevBuf bsrc, bdst, bk, bk2, btemp, bkeep, bpos;
   const int32_t *d_src = src, *d_dst = dst;
   if (!on_device && m > 0) {
     int32_t *a = static_cast<int32_t *>(bsrc.ensure(4 * m));
@@ -658,31 +721,34 @@ Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int6
   WCC_CUDA(cudaMemsetAsync(d_off, 0, 8 * (n + 1), s));
   int64_t nnz = 0;
   if (m > 0) {
+    // the columns get room for every directed entry, so nothing has to be
+    // read back before the end: one read of {error, nnz} closes the build
     uint64_t *k1 = static_cast<uint64_t *>(bk.ensure(8 * n2));
     uint64_t *k2 = static_cast<uint64_t *>(bk2.ensure(8 * n2));
     void *temp = btemp.ensure(std::max(radix_temp_bytes(n2), scan_temp_bytes(n + 1)) + 64);
-    unsigned *d_err = static_cast<unsigned *>(bkeep.ensure(4 * (n2 + 1)));
+    uint32_t *keep = static_cast<uint32_t *>(bkeep.ensure(4 * (n2 + 2)));
+    uint32_t *pos = static_cast<uint32_t *>(bpos.ensure(4 * (n2 + 1)));
+    unsigned *d_err = keep + n2 + 1;
     WCC_CUDA(cudaMemsetAsync(d_err, 0, 4, s));
     k_edge_keys<<<blocks_for(m), TB, 0, s>>>(d_src, d_dst, m, n, b, k1, d_err); note_launch();
     WCC_CUDA(cudaGetLastError());
-    unsigned err = read_back(d_err, s);
-    if (err) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
     uint64_t *sorted = k1;
     // valid keys are (u << b) | v < 2^(2b) - 1 (u != v); dropped self-loops
     // carry all ones, so sorting on the low 2b bits puts them last
     if (radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, s)) sorted = k2;
-    uint32_t *keep = reinterpret_cast<uint32_t *>(d_err);
-    uint32_t *pos = static_cast<uint32_t *>(bpos.ensure(4 * (n2 + 1)));
     k_unique_flags<<<blocks_for(n2), TB, 0, s>>>(sorted, n2, keep, ~0ull); note_launch();
     exclusive_scan_u32(keep, pos, n2, pos + n2, temp, s);
-    uint32_t tot = read_back(pos + n2, s);
-    nnz = tot;
-    int32_t *d_adj = static_cast<int32_t *>(g->adj.ensure(4 * std::max<int64_t>(nnz, 1)));
-    int64_t *deg = static_cast<int64_t *>(bdeg.ensure(8 * (n + 1)));
-    WCC_CUDA(cudaMemsetAsync(deg, 0, 8 * (n + 1), s));
-    k_compact_edges<<<blocks_for(n2), TB, 0, s>>>(sorted, keep, pos, n2, b, d_adj, deg); note_launch();
-    exclusive_scan_i64(deg, d_off, n + 1, nullptr, temp, s);
+    int32_t *d_adj = static_cast<int32_t *>(g->adj.ensure(4 * n2));
+    k_compact_edges<<<blocks_for(n2), TB, 0, s>>>(sorted, keep, pos, n2, b, d_adj, d_off);
+    note_launch();
+    exclusive_scan_i64(d_off, d_off, n + 1, nullptr, temp, s);
     WCC_CUDA(cudaGetLastError());
+    uint32_t tail[2] = {0, 0};
+    WCC_CUDA(cudaMemcpyAsync(&tail[0], d_err, 4, cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaMemcpyAsync(&tail[1], pos + n2, 4, cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaStreamSynchronize(s));
+    if (tail[0]) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
+    nnz = tail[1];
   } else {
     g->adj.ensure(4);
   }

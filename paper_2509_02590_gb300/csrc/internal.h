@@ -19,6 +19,7 @@ namespace wccg {
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  int dev = -1;  // device the block belongs to
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
