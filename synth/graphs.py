@@ -44,7 +44,10 @@ def _dedup(n: int, u: np.ndarray, v: np.ndarray):
     keep = u != v
     a = np.minimum(u[keep], v[keep])
     b = np.maximum(u[keep], v[keep])
-    key = np.unique(a * n + b)
+    key = a * n + b
+    key.sort()
+    if len(key):
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     return (key // n).astype(np.int32), (key % n).astype(np.int32)
 
 
