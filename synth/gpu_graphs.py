@@ -8,8 +8,9 @@ refinement's arithmetic.  The same recipe as ``graphs.dc_planted``: Chung-Lu
 weights with a power-law distribution, power-law cluster sizes, a fraction of
 chain clusters cut into 2-4 parts joined by 1-2 bridges, intra edges spread
 over the edge groups in proportion to their weight (capped at density 0.5)
-with endpoints drawn in proportion to the weights inside the group, inter
-edges with endpoints drawn in proportion to the weights over the whole graph
+with endpoints drawn in proportion to the weights inside the group, the rest
+of the m drawn edges (including what the density cap refused) as inter edges
+with endpoints drawn in proportion to the weights over the whole graph
 (same-cluster pairs dropped), then a random relabelling of vertices and label
 values, and removal of loops and repeats.
 """
@@ -127,8 +128,9 @@ def dc_planted_gpu(n: int, m: int, seed: int = 0, deg_exp: float = 2.2, max_deg:
         iv = _draw(torch, gen, cw, lo, hi, len(g_of))
         keys.append(_pack(torch, iu, iv, n))
         done = hi_e
-    # inter edges
-    m_out = int(round((1.0 - f_in) * m * draw_factor))
+    # inter edges: the rest of the draw (intra edges a density cap refused
+    # move here, so the total stays m * draw_factor)
+    m_out = max(0, int(round(m * draw_factor)) - total)
     done = 0
     zero = torch.zeros((), dtype=torch.long, device=device)
     top = torch.full((), n, dtype=torch.long, device=device)
@@ -158,14 +160,27 @@ def dc_planted_gpu(n: int, m: int, seed: int = 0, deg_exp: float = 2.2, max_deg:
     key = mn * n + mx
     del mn, mx
     key = key[(key // n) != (key % n)]
-    key, _ = torch.sort(key)
-    if key.numel():
-        key = key[torch.cat([torch.ones(1, dtype=torch.bool, device=device), key[1:] != key[:-1]])]
-    src = (key // n).int()
-    dst = (key % n).int()
+    # sort and drop repeats in key-range buckets (a sort takes at most 2^31
+    # elements; equal keys always share a bucket)
+    nb = max(1, -(-key.numel() // (1 << 30)))
+    span = -(-(n * n) // nb)
+    srcs, dsts = [], []
+    for bi in range(nb):
+        part = key[(key >= bi * span) & (key < (bi + 1) * span)] if nb > 1 else key
+        part, _ = torch.sort(part)
+        if part.numel():
+            part = part[torch.cat([torch.ones(1, dtype=torch.bool, device=device),
+                                   part[1:] != part[:-1]])]
+        srcs.append((part // n).int())
+        dsts.append((part % n).int())
+        del part
     del key
+    src = torch.cat(srcs)
+    dst = torch.cat(dsts)
+    del srcs, dsts
     return GpuWorkload("dc_planted_gpu", n, src, dst, lab, min_size,
                        {"clusters": k, "chains": int(is_chain.sum()), "w_min": wmin,
+                        "intra_drawn": total, "inter_drawn": m_out,
                         "size_exp": size_exp, "seed": seed,
                         "cluster_sizes": sizes, "chain_clusters": np.nonzero(is_chain)[0],
                         "label_of_cluster": newv.cpu().numpy()})
@@ -183,7 +198,7 @@ def dcpp_10m(seed: int = 0, device: str = "cuda") -> GpuWorkload:
     5% chain clusters of 2-4 parts."""
     return dc_planted_gpu(10_000_000, 200_000_000, seed=seed, deg_exp=2.2, size_exp=1.8,
                           size_min=10, size_max=50_000, f_in=0.8, chain_frac=0.05,
-                          chain_parts=(2, 4), device=device, draw_factor=1.36)
+                          chain_parts=(2, 4), device=device, draw_factor=1.285)
 
 
 def dcpp_100m(seed: int = 0, device: str = "cuda") -> GpuWorkload:
@@ -194,4 +209,4 @@ def dcpp_100m(seed: int = 0, device: str = "cuda") -> GpuWorkload:
     return dc_planted_gpu(100_000_000, 2_000_000_000, seed=seed, deg_exp=2.1, max_deg=200_000,
                           size_exp=None, size_mean=20.0, size_min=10, size_max=100_000,
                           f_in=0.8, chain_frac=0.03, chain_parts=(2, 2), device=device,
-                          draw_factor=1.25)
+                          draw_factor=1.19)

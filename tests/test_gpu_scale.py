@@ -76,7 +76,7 @@ def test_dcpp_10m_sampled_parity():
     wcc = _wcc()
     from synth import gpu_graphs
     w = gpu_graphs.dcpp_10m(seed=0)
-    assert w.n == 10_000_000 and w.m > 180_000_000
+    assert w.n == 10_000_000 and 190_000_000 < w.m < 210_000_000
     ref, got, ost, st, ns = _sampled_parity(wcc, w)
     assert st["in_clusters"] == w.meta["clusters"]
     assert ost["splits"] > 0            # the sample contains clusters that split
@@ -88,6 +88,6 @@ def test_dcpp_100m_sampled_parity():
     wcc = _wcc()
     from synth import gpu_graphs
     w = gpu_graphs.dcpp_100m(seed=0)
-    assert w.n == 100_000_000 and w.m > 1_500_000_000
+    assert w.n == 100_000_000 and 1_900_000_000 < w.m < 2_100_000_000
     ref, got, ost, st, ns = _sampled_parity(wcc, w, n_largest=2, n_chains=30, n_random=300)
     assert np.array_equal(got, ref), f"{int((got != ref).sum())} of {ns} sampled vertices differ"
