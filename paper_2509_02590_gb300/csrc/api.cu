@@ -104,18 +104,7 @@ namespace {
 
 constexpr int TB = 256;
 
-inline unsigned blocks_for(int64_t n, int per = TB) {
-  int64_t b = (n + per - 1) / per;
-  if (b < 1) b = 1;
-  if (b > 0x7fffffff) b = 0x7fffffff;
-  return (unsigned)b;
-}
-
-int bitlen_u64(uint64_t x) {
-  int b = 0;
-  while (x) { ++b; x >>= 1; }
-  return b;
-}
+inline unsigned blocks_for(int64_t n, int per = TB) { return grid_for(n, per); }
 
 // ---------------------------------------------------------------- CSR checks
 // Warp per vertex: offsets in range and non-decreasing, ids in [0, n), no
@@ -190,148 +179,6 @@ __global__ void k_compact_edges(const uint64_t *__restrict__ keys, const uint32_
   atomicAdd((unsigned long long *)&deg[u], 1ull);
 }
 
-// ---------------------------------------------------------------- membership
-struct SeedInfo {
-  unsigned long long max_n;     // largest kept cluster
-  unsigned long long max_dsum;  // largest degree sum of a kept cluster
-  long long clusters;           // K: distinct labels
-  long long skip;               // unclustered vertices (they sort first)
-  unsigned err;                 // DERR_* bits
-  unsigned maxkey;              // largest label + 1
-  unsigned kept;                // clusters with >= min_size members
-  unsigned pad;
-};
-
-__global__ void k_make_keys(const int32_t *__restrict__ lab, int64_t n, uint32_t *keys,
-                            uint32_t *vals, unsigned *maxkey, unsigned *err) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned k = 0;
-  if (i < n) {
-    int32_t c = lab[i];
-    if (c < -1) atomicOr(err, DERR_INVALID);
-    k = c < 0 ? 0u : (unsigned)c + 1u;
-    keys[i] = k;
-    vals[i] = (uint32_t)i;
-  }
-  k = warp_max(k);
-  if ((threadIdx.x & 31) == 0 && k) atomicMax(maxkey, k);
-}
-
-__global__ void k_heads(const uint32_t *__restrict__ sk, int64_t n, uint32_t *head) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  head[i] = (sk[i] != 0 && (i == 0 || sk[i - 1] != sk[i])) ? 1u : 0u;
-}
-
-// cstart[c] = first sorted position of cluster c, cstart[K] = n; also
-// records K and the number of unclustered vertices (they sort first).
-__global__ void k_starts(const uint32_t *__restrict__ head, const uint32_t *__restrict__ hidx,
-                         int64_t n, int64_t *cstart, SeedInfo *info) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t K = hidx[n];
-  if (i < n && head[i]) {
-    cstart[hidx[i]] = i;
-    if (hidx[i] == 0) info->skip = i;
-  }
-  if (i == 0) {
-    cstart[K] = n;
-    info->clusters = K;
-    if (K == 0) info->skip = n;
-  }
-}
-
-// degree of each vertex in sorted order (for the per-cluster degree sums)
-__global__ void k_sorted_deg(const uint32_t *__restrict__ sv, const int64_t *__restrict__ off,
-                             int64_t n, int64_t *dg) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t v = sv[i];
-  dg[i] = off[v + 1] - off[v];
-}
-
-
-
-__global__ void k_keep(const int64_t *__restrict__ cstart, const uint32_t *__restrict__ Kp,
-                       int64_t cap, int min_size, uint32_t *keep,
-                       const int64_t *__restrict__ pdeg, SeedInfo *info) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t K = *Kp;
-  unsigned long long sz = 0, ds = 0;
-  if (c < cap && c >= K) keep[c] = 0u;
-  if (c < K) {
-    sz = (unsigned long long)(cstart[c + 1] - cstart[c]);
-    bool k = (int64_t)sz >= min_size;
-    keep[c] = k ? 1u : 0u;
-    if (k) ds = (unsigned long long)(pdeg[cstart[c + 1]] - pdeg[cstart[c]]);
-    else sz = 0;
-  }
-  sz = warp_max(sz);
-  ds = warp_max(ds);
-  if ((threadIdx.x & 31) == 0) {
-    if (sz) atomicMax(&info->max_n, sz);
-    if (ds) atomicMax(&info->max_dsum, ds);
-  }
-}
-
-// Sort keys putting kept clusters first, larger ones earlier (longest work
-// first); unkept clusters get the largest key.
-__global__ void k_size_keys(const int64_t *__restrict__ cstart, const uint32_t *__restrict__ keep,
-                            int64_t K, uint32_t max_n, uint32_t *keys, uint32_t *vals) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= K) return;
-  uint32_t sz = (uint32_t)(cstart[c + 1] - cstart[c]);
-  keys[c] = keep[c] ? max_n - sz : max_n + 1;
-  vals[c] = (uint32_t)c;
-}
-
-__global__ void k_invert(const uint32_t *__restrict__ order, int64_t nkept, uint32_t *qidx) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nkept) qidx[order[i]] = (uint32_t)i;
-}
-
-__global__ void k_seed(const int64_t *__restrict__ cstart, const uint32_t *__restrict__ keep,
-                       const uint32_t *__restrict__ qidx, int64_t K, int64_t skip, QSlot *ring,
-                       uint64_t cap) {
-  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= K || !keep[c]) return;
-  uint64_t q = qidx[c];
-  QSlot *s = &ring[q % cap];
-  s->item.vbeg = cstart[c] - skip;
-  s->item.n = (int32_t)(cstart[c + 1] - cstart[c]);
-  s->item.flags = ITEM_TOP;
-  s->seq = q;
-}
-
-// pool[i - skip] = sorted vertex; slot[v] = (queue index << 32) | rank
-__global__ void k_pool_slots(const uint32_t *__restrict__ sk, const uint32_t *__restrict__ sv,
-                             const uint32_t *__restrict__ head, const uint32_t *__restrict__ hidx,
-                             const int64_t *__restrict__ cstart,
-                             const uint32_t *__restrict__ keep, const uint32_t *__restrict__ qidx,
-                             int64_t n, int64_t skip, int32_t *pool,
-                             unsigned long long *slot) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || i < skip) return;
-  uint32_t v = sv[i];
-  pool[i - skip] = (int32_t)v;
-  int64_t c = (int64_t)hidx[i] + head[i] - 1;  // inclusive head count - 1
-  if (keep[c]) slot[v] = ((unsigned long long)qidx[c] << 32) | (unsigned)(i - cstart[c]);
-  (void)sk;
-}
-
-// ---------------------------------------------------------------- output
-__global__ void k_out_flags(const int32_t *__restrict__ lmin, int64_t n, uint32_t *flag) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) flag[i] = lmin[i] == (int32_t)i ? 1u : 0u;
-}
-
-__global__ void k_out_final(const int32_t *__restrict__ lmin, const uint32_t *__restrict__ rank,
-                            int64_t n, int32_t *out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t r = lmin[i];
-  out[i] = r >= 0 ? (int32_t)rank[r] : -1;
-}
-
 // ---------------------------------------------------------------- helpers
 struct DeviceGuard {
   int prev = -1;
@@ -358,15 +205,7 @@ int current_device() {
   return dev;
 }
 
-void check_derr(unsigned err, const char *what) {
-  if (!err) return;
-  if (err & DERR_INVALID) fail(WCC_ERR_INVALID, std::string(what) + ": malformed input");
-  if (err & DERR_TIMEOUT)
-    fail(WCC_ERR_TIMEOUT, std::string(what) + ": a device-side queue wait exceeded its limit");
-  if (err & DERR_CAPACITY)
-    fail(WCC_ERR_INTERNAL, std::string(what) + ": an internal capacity bound was exceeded");
-  fail(WCC_ERR_INTERNAL, std::string(what) + ": internal consistency check failed");
-}
+void check_derr(unsigned err, const char *what) { check_device_error(err, what); }
 
 // Limit of every device-side queue wait (WCC_WAIT_LIMIT_MS, default 30 s):
 // a CTA that waits longer sets DERR_TIMEOUT and leaves, so a fault in the
@@ -390,13 +229,6 @@ size_t refine_smem_bytes_config(int device) {
   return (size_t)kb * 1024;
 }
 
-template <typename T>
-T read_back(const T *dev, cudaStream_t s) {
-  T h;
-  WCC_CUDA(cudaMemcpyAsync(&h, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
-  WCC_CUDA(cudaStreamSynchronize(s));
-  return h;
-}
 
 // Writes the per-item profile of the last refinement as CSV (appending).
 void dump_item_profile(const RefineParams &p, const char *path, cudaStream_t s) {
@@ -419,12 +251,7 @@ void dump_item_profile(const RefineParams &p, const char *path, cudaStream_t s) 
   fclose(f);
 }
 
-enum Ws {
-  W_KEYS, W_VALS, W_KEYS2, W_VALS2, W_TEMP, W_HEAD, W_HIDX, W_CSTART, W_PDEG, W_KEEP, W_QIDX,
-  W_POOL, W_SLOT, W_LMIN, W_RING, W_CTR, W_SLAB, W_INFO, W_OUT, W_IN, W_FLAG, W_RANK, W_DG,
-  W_OK1, W_OV1, W_OK2, W_OV2, W_COUNT
-};
-static_assert(W_COUNT <= 32, "workspace slots");
+
 
 struct Timer {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -448,16 +275,25 @@ struct Timer {
   }
 };
 
-void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, int32_t min_size,
-              int32_t mode, int32_t *lab_out, int on_device, cudaStream_t s, wcc_stats *stats) {
-  auto t_start = std::chrono::steady_clock::now();
-  const int64_t n = g->n;
+// Validates a threshold rule and min_size; returns the rule to use.
+wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule) {
   wcc_threshold_rule r = rule ? *rule : wcc_threshold_rule{WCC_RULE_LOG10, 0, 0, 1};
   if (r.kind < WCC_RULE_LOG10 || r.kind > WCC_RULE_LINEAR)
     fail(WCC_ERR_INVALID, "unknown threshold rule kind " + std::to_string(r.kind));
   if (r.kind == WCC_RULE_LINEAR &&
       (r.den <= 0 || r.num < 0 || r.den >= (1ll << 31) || r.num >= (1ll << 31)))
     fail(WCC_ERR_INVALID, "LINEAR rule needs 0 <= num < 2^31 and 0 < den < 2^31");
+  return r;
+}
+
+enum RunBuf { R_IN, R_OUT, R_POOL, R_SLOT, R_LMIN, R_RING, R_CTR, R_SLAB, R_REQ, R_COUNT };
+static_assert(R_COUNT <= 16, "run buffers");
+
+void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, int32_t min_size,
+              int32_t mode, int32_t *lab_out, int on_device, cudaStream_t s, wcc_stats *stats) {
+  auto t_start = std::chrono::steady_clock::now();
+  const int64_t n = g->n;
+  const wcc_threshold_rule r = checked_rule(rule);
   if (mode != WCC_MODE_BATCHED && mode != WCC_MODE_PLAIN)
     fail(WCC_ERR_INVALID, "unknown mode " + std::to_string(mode));
   if (min_size < 2) min_size = 2;
@@ -465,129 +301,65 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     fail(WCC_ERR_INVALID, "clustering_in and clustering_out must not be NULL");
   if (lab_in == lab_out) fail(WCC_ERR_INVALID, "clustering_out may not alias clustering_in");
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  if (n == 0) {
-    if (stats) stats->ms_total = 0;
-    return;
-  }
+  if (n == 0) return;
   Timer tm(stats != nullptr);
-  DevBuf *ws = g->ws;
+  DevBuf *rb = g->rb;
 
   // input labels on the device
   const int32_t *d_in = lab_in;
   if (!on_device) {
-    int32_t *p = static_cast<int32_t *>(ws[W_IN].ensure(4 * n));
+    int32_t *p = static_cast<int32_t *>(rb[R_IN].ensure(4 * n));
     WCC_CUDA(cudaMemcpyAsync(p, lab_in, 4 * n, cudaMemcpyHostToDevice, s));
     d_in = p;
   }
   tm.mark(0, s);
 
-  // ---- a2: group vertices by input label (stable radix sort on label+1)
-  uint32_t *keys = static_cast<uint32_t *>(ws[W_KEYS].ensure(4 * n));
-  uint32_t *vals = static_cast<uint32_t *>(ws[W_VALS].ensure(4 * n));
-  uint32_t *keys2 = static_cast<uint32_t *>(ws[W_KEYS2].ensure(4 * n));
-  uint32_t *vals2 = static_cast<uint32_t *>(ws[W_VALS2].ensure(4 * n));
-  size_t temp_b = std::max(radix_temp_bytes(n), scan_temp_bytes(n + 1));
-  void *temp = ws[W_TEMP].ensure(temp_b);
-  SeedInfo *info = static_cast<SeedInfo *>(ws[W_INFO].ensure(sizeof(SeedInfo)));
-  WCC_CUDA(cudaMemsetAsync(info, 0, sizeof(SeedInfo), s));
-  k_make_keys<<<blocks_for(n), TB, 0, s>>>(d_in, n, keys, vals, &info->maxkey, &info->err); note_launch();
-  WCC_CUDA(cudaGetLastError());
-  SeedInfo h0 = read_back(info, s);
-  if (h0.err) check_derr(h0.err, "clustering_in");
-  const int bits = bitlen_u64(h0.maxkey);
-  uint32_t *sk = keys, *sv = vals;
-  if (radix_sort_pairs_u32(keys, vals, keys2, vals2, n, bits, temp, s)) {
-    sk = keys2;
-    sv = vals2;
-  }
-  uint32_t *head = static_cast<uint32_t *>(ws[W_HEAD].ensure(4 * (n + 1)));
-  uint32_t *hidx = static_cast<uint32_t *>(ws[W_HIDX].ensure(4 * (n + 1)));
-  k_heads<<<blocks_for(n), TB, 0, s>>>(sk, n, head); note_launch();
-  WCC_CUDA(cudaGetLastError());
-  // hidx[n] receives the number of distinct labels K; arrays indexed by
-  // cluster are sized by n so that K need not be read back here
-  exclusive_scan_u32(head, hidx, n, hidx + n, temp, s);
-  int64_t *cstart = static_cast<int64_t *>(ws[W_CSTART].ensure(8 * (n + 1)));
-  k_starts<<<blocks_for(n), TB, 0, s>>>(head, hidx, n, cstart, info); note_launch();
+  // ---- a2: group vertices by input label
+  const GroupInfo gi = group_by_label(g->off.as<int64_t>(), n, d_in, min_size, g->ws, s);
 
-  // per-cluster degree sums (prefix sums of degrees in sorted order)
-  int64_t *dg = static_cast<int64_t *>(ws[W_DG].ensure(8 * (n + 1)));
-  int64_t *pdeg = static_cast<int64_t *>(ws[W_PDEG].ensure(8 * (n + 1)));
-  uint32_t *keep = static_cast<uint32_t *>(ws[W_KEEP].ensure(4 * (n + 1)));
-  uint32_t *qidx = static_cast<uint32_t *>(ws[W_QIDX].ensure(4 * (n + 1)));
-  k_sorted_deg<<<blocks_for(n), TB, 0, s>>>(sv, g->off.as<int64_t>(), n, dg); note_launch();
-  WCC_CUDA(cudaMemsetAsync(dg + n, 0, 8, s));
-  exclusive_scan_i64(dg, pdeg, n + 1, nullptr, temp, s);
-  k_keep<<<blocks_for(n), TB, 0, s>>>(cstart, hidx + n, n, min_size, keep, pdeg, info); note_launch();
-  exclusive_scan_u32(keep, qidx, n, &info->kept, temp, s);
-  WCC_CUDA(cudaGetLastError());
-  SeedInfo hi = read_back(info, s);
-  const int64_t K = hi.clusters;
-  const int64_t skip = hi.skip;
-  const int64_t nkept = (int64_t)hi.kept;
-  {
-    if (nkept > 1) {
-      // queue order: largest input clusters first (qidx = rank by size)
-      uint32_t *ok1 = static_cast<uint32_t *>(ws[W_OK1].ensure(4 * K));
-      uint32_t *ov1 = static_cast<uint32_t *>(ws[W_OV1].ensure(4 * K));
-      uint32_t *ok2 = static_cast<uint32_t *>(ws[W_OK2].ensure(4 * K));
-      uint32_t *ov2 = static_cast<uint32_t *>(ws[W_OV2].ensure(4 * K));
-      k_size_keys<<<blocks_for(K), TB, 0, s>>>(cstart, keep, K, (uint32_t)hi.max_n, ok1, ov1);
-      note_launch();
-      uint32_t *ov = ov1;
-      if (radix_sort_pairs_u32(ok1, ov1, ok2, ov2, K, bitlen_u64(hi.max_n + 1), temp, s)) ov = ov2;
-      k_invert<<<blocks_for(nkept), TB, 0, s>>>(ov, nkept, qidx);
-      note_launch();
-      WCC_CUDA(cudaGetLastError());
-    }
-  }
-
-  // ---- queue, pool, slots
+  // ---- queue, pool, slots, the one-entry request table
   const int dev = g->device;
   const size_t smem_bytes = refine_smem_bytes_config(dev);
-  const int max_ctas = refine_max_ctas(dev, smem_bytes);
-  const int grid = max_ctas;
+  const int grid = refine_max_ctas(dev, smem_bytes);
   const uint64_t cap = (uint64_t)n + 2ull * grid + 1024;
-  int32_t *pool = static_cast<int32_t *>(ws[W_POOL].ensure(4 * std::max<int64_t>(n - skip, 1)));
-  auto *slot = static_cast<unsigned long long *>(ws[W_SLOT].ensure(8 * n));
-  auto *lmin = static_cast<int32_t *>(ws[W_LMIN].ensure(4 * n));
-  auto *ring = static_cast<QSlot *>(ws[W_RING].ensure(sizeof(QSlot) * cap));
-  auto *ctr = static_cast<RunCounters *>(ws[W_CTR].ensure(sizeof(RunCounters)));
+  int32_t *pool = static_cast<int32_t *>(rb[R_POOL].ensure(4 * std::max<int64_t>(n - gi.skip, 1)));
+  auto *slot = static_cast<unsigned long long *>(rb[R_SLOT].ensure(8 * n));
+  auto *lmin = static_cast<int32_t *>(rb[R_LMIN].ensure(4 * n));
+  auto *ring = static_cast<QSlot *>(rb[R_RING].ensure(sizeof(QSlot) * cap));
+  auto *ctr = static_cast<RunCounters *>(rb[R_CTR].ensure(sizeof(RunCounters)));
+  auto *req = static_cast<ReqCtx *>(rb[R_REQ].ensure(sizeof(ReqCtx)));
   WCC_CUDA(cudaMemsetAsync(slot, 0xff, 8 * n, s));
   WCC_CUDA(cudaMemsetAsync(lmin, 0xff, 4 * n, s));
   WCC_CUDA(cudaMemsetAsync(ctr, 0, sizeof(RunCounters), s));
-  if (nkept > 0) {
+  ReqCtx hreq{};
+  hreq.off = g->off.as<int64_t>();
+  hreq.adj = g->adj.as<int32_t>();
+  hreq.n_vertices = n;
+  hreq.pool = pool;
+  hreq.slot = slot;
+  hreq.label_min = lmin;
+  hreq.rule_kind = r.kind;
+  hreq.min_size = min_size;
+  hreq.rule_num = r.num;
+  hreq.rule_den = r.den;
+  WCC_CUDA(cudaMemcpyAsync(req, &hreq, sizeof(hreq), cudaMemcpyHostToDevice, s));
+  if (gi.kept > 0) {
     WCC_CUDA(cudaMemsetAsync(ring, 0xff, sizeof(QSlot) * cap, s));
-    k_seed<<<blocks_for(K), TB, 0, s>>>(cstart, keep, qidx, K, skip, ring, cap); note_launch();
-    k_pool_slots<<<blocks_for(n), TB, 0, s>>>(sk, sv, head, hidx, cstart, keep, qidx, n, skip,
-                                              pool, slot); note_launch();
-    WCC_CUDA(cudaGetLastError());
-    RunCounters c0{};
-    c0.tail = (unsigned long long)nkept;
-    c0.pending = nkept;
-    WCC_CUDA(cudaMemcpyAsync(ctr, &c0, sizeof(c0), cudaMemcpyHostToDevice, s));
+    seed_items(gi, n, g->ws, 0, req, pool, slot, ring, cap, ctr, s);
   }
   tm.mark(1, s);
 
   // ---- refinement
-  if (nkept > 0) {
-    size_t need = item_workspace_bytes((int64_t)hi.max_n, (int64_t)hi.max_dsum);
+  if (gi.kept > 0) {
+    size_t need = item_workspace_bytes(gi.max_n, gi.max_dsum);
     size_t slab_bytes = need > smem_bytes ? ((need + 255) & ~(size_t)255) : 256;
     RefineParams p{};
-    p.off = g->off.as<int64_t>();
-    p.adj = g->adj.as<int32_t>();
-    p.n_vertices = n;
-    p.pool = pool;
-    p.slot = slot;
-    p.label_min = lmin;
+    p.reqs = req;
     p.ring = ring;
     p.ring_cap = cap;
     p.ctr = ctr;
-    p.rule_kind = r.kind;
-    p.rule_num = r.num;
-    p.rule_den = r.den;
-    p.min_size = min_size;
     p.wait_limit_ns = wait_limit_ns();
+    p.idle_limit_ns = 0;
     p.smem_bytes = smem_bytes;
     p.slab_bytes = slab_bytes;
     // optional per-item profile (WCC_PROFILE_ITEMS=<csv path>)
@@ -602,13 +374,13 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
       WCC_CUDA(cudaMemsetAsync(pb, 0, 64, s));
     }
     if (mode == WCC_MODE_BATCHED) {
-      p.slab = static_cast<char *>(ws[W_SLAB].ensure(slab_bytes * (size_t)grid));
+      p.slab = static_cast<char *>(rb[R_SLAB].ensure(slab_bytes * (size_t)grid));
       p.single_item = 0;
       launch_refine(p, grid, true, s);
     } else {
-      p.slab = static_cast<char *>(ws[W_SLAB].ensure(slab_bytes));
+      p.slab = static_cast<char *>(rb[R_SLAB].ensure(slab_bytes));
       p.single_item = 1;
-      unsigned long long tail = (unsigned long long)nkept;
+      unsigned long long tail = (unsigned long long)gi.kept;
       for (unsigned long long j = 0; j < tail; ++j) {
         p.single_index = j;
         launch_refine(p, 1, false, s);
@@ -623,34 +395,31 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
   }
   tm.mark(2, s);
   RunCounters hc{};
-  if (nkept > 0) {
+  ReqCtx hr{};
+  if (gi.kept > 0) {
     hc = read_back(ctr, s);
     check_derr(hc.error, "refinement");
+    hr = read_back(req, s);
   }
 
   // ---- a9: ids = rank of each accepted cluster's smallest vertex
-  uint32_t *flag = static_cast<uint32_t *>(ws[W_FLAG].ensure(4 * n));
-  uint32_t *rank = static_cast<uint32_t *>(ws[W_RANK].ensure(4 * n));
   int32_t *d_out = lab_out;
-  if (!on_device) d_out = static_cast<int32_t *>(ws[W_OUT].ensure(4 * n));
-  k_out_flags<<<blocks_for(n), TB, 0, s>>>(lmin, n, flag); note_launch();
-  exclusive_scan_u32(flag, rank, n, nullptr, temp, s);
-  k_out_final<<<blocks_for(n), TB, 0, s>>>(lmin, rank, n, d_out); note_launch();
-  WCC_CUDA(cudaGetLastError());
+  if (!on_device) d_out = static_cast<int32_t *>(rb[R_OUT].ensure(4 * n));
+  number_clusters(lmin, n, d_out, g->ws, s);
   tm.mark(3, s);
   if (!on_device) WCC_CUDA(cudaMemcpyAsync(lab_out, d_out, 4 * n, cudaMemcpyDeviceToHost, s));
   WCC_CUDA(cudaStreamSynchronize(s));
 
   if (stats) {
-    stats->in_clusters = K;
-    stats->out_clusters = hc.accepted;
-    stats->items = hc.items;
-    stats->splits = hc.splits;
-    stats->peeled = hc.peeled;
-    stats->ni_passes = hc.ni_passes;
-    stats->sw_phases = hc.sw_phases;
-    stats->max_item = (int64_t)hi.max_n;
-    stats->alg_bytes = hc.alg_bytes + 16 * n;
+    stats->in_clusters = gi.clusters;
+    stats->out_clusters = hr.accepted;
+    stats->items = hr.items;
+    stats->splits = hr.splits;
+    stats->peeled = hr.peeled;
+    stats->ni_passes = hr.ni_passes;
+    stats->sw_phases = hr.sw_phases;
+    stats->max_item = gi.max_n;
+    stats->alg_bytes = hr.alg_bytes;
     stats->ms_membership = tm.ms(0, 1);
     stats->ms_refine = tm.ms(1, 2);
     stats->ms_output = tm.ms(2, 3);
@@ -715,7 +484,7 @@ Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int6
     d_src = a;
     d_dst = b;
   }
-  const int b = std::max(1, bitlen_u64(n > 0 ? (uint64_t)(n - 1) : 0));
+  const int b = (int)std::max<int64_t>(1, bitlen_u64(n > 0 ? (uint64_t)(n - 1) : 0));
   const int64_t n2 = 2 * m;
   int64_t *d_off = static_cast<int64_t *>(g->off.ensure(8 * (n + 1)));
   WCC_CUDA(cudaMemsetAsync(d_off, 0, 8 * (n + 1), s));
@@ -819,7 +588,7 @@ void build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64
   WCC_CUDA(cudaMemsetAsync(err, 0, 16, s));
   int64_t nnz = 0;
   if (m > 0) {
-    const int b = std::max(1, bitlen_u64(n > 0 ? (uint64_t)(n - 1) : 0));
+    const int b = (int)std::max<int64_t>(1, bitlen_u64(n > 0 ? (uint64_t)(n - 1) : 0));
     k_edge_keys<<<blocks_for(m), TB, 0, s>>>(src, dst, m, n, b, k1, err); note_launch();
     WCC_CUDA(cudaGetLastError());
     if (read_back(err, s)) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");

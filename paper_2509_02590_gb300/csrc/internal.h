@@ -53,6 +53,13 @@ bool radix_sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, ui
 bool radix_sort_keys_u64(uint64_t *keys, uint64_t *keys_alt, int64_t n, int bits, void *temp,
                          cudaStream_t s);
 
+// Per-request workspace of the pipeline stages: grown on demand, kept
+// between runs; sk/sv remember where group_by_label() left its sort.
+struct Workspace {
+  DevBuf b[24];
+  uint32_t *sk = nullptr, *sv = nullptr;
+};
+
 // ---- graph ----------------------------------------------------------------
 struct Graph {
   int64_t n = 0;
@@ -61,18 +68,36 @@ struct Graph {
   DevBuf off;  // int64 [n+1]
   DevBuf adj;  // int32 [nnz]
   std::mutex run_mutex;  // wcc_run calls on one graph are serialised
-  // per-run workspace, kept between runs
-  DevBuf ws[32];
+  // per-run buffers, kept between runs
+  Workspace ws;
+  DevBuf rb[16];
 };
 
 // ---- refine.cu -------------------------------------------------------------
 // Work item of the device queue.
 struct Item {
-  int64_t vbeg;   // start of the item's vertex list in the vertex pool
+  int64_t vbeg;   // start of the item's vertex list in its request's vertex pool
   int32_t n;      // vertices
-  uint32_t flags; // ITEM_TOP: an input cluster (CCR first, Algorithm 1)
+  uint16_t flags; // ITEM_TOP: an input cluster (CCR first, Algorithm 1)
+  uint16_t req;   // request it belongs to (index into the request table)
 };
-enum : uint32_t { ITEM_TOP = 1u };
+enum : uint16_t { ITEM_TOP = 1u };
+
+// One refinement request: its graph, its per-vertex state and its counters.
+// wcc_run uses one; a server keeps a table of them for the requests it has
+// admitted, and the refinement kernel reads the entry an item names.
+struct ReqCtx {
+  const int64_t *off;          // graph CSR
+  const int32_t *adj;
+  int64_t n_vertices;
+  int32_t *pool;               // vertex lists of all the request's items
+  unsigned long long *slot;    // per vertex: (queue index << 32) | local id, ~0 = none
+  int32_t *label_min;          // per vertex: smallest vertex id of its accepted cluster, or -1
+  int32_t rule_kind, min_size;
+  int64_t rule_num, rule_den;
+  long long pending;           // published but unfinished items of this request
+  long long items, splits, peeled, ni_passes, sw_phases, accepted, alg_bytes;
+};
 
 // A ring slot: the item plus the queue sequence number it was published
 // under (seq == index means "ready").
@@ -84,12 +109,12 @@ struct QSlot {
 // Device counters of one refinement run.
 struct RunCounters {
   unsigned long long head;     // next queue index to claim
-  unsigned long long tail;     // next queue index to publish
-  long long pending;           // published but unfinished items
+  unsigned long long tail;     // next queue index to reserve (published once its seq is set)
+  long long pending;           // reserved but unfinished items, all requests
   unsigned int error;          // DERR_* bits
   unsigned int err_info;       // first failing detail (debug aid)
-  long long items, splits, peeled, ni_passes, sw_phases, accepted;
-  long long alg_bytes;         // bytes of adjacency + slot gathers actually read
+  int open;                    // 1 while a server may still add work (kernel idles instead of exiting)
+  int pad;
 };
 
 // Optional per-item profile record (phase durations in SM cycles: load,
@@ -103,19 +128,13 @@ struct ItemProf {
 };
 
 struct RefineParams {
-  const int64_t *off;
-  const int32_t *adj;
-  int64_t n_vertices;
-  int32_t *pool;              // vertex lists of all items (length = clustered vertices)
-  unsigned long long *slot;   // per vertex: (item seq << 32) | local id, ~0 = none
-  int32_t *label_min;         // per vertex: smallest vertex id of its accepted cluster, or -1
+  ReqCtx *reqs;               // request table (device)
+  int *done_flags;            // optional, host-mapped: set to 1 when a request's last item ends
   QSlot *ring;
   uint64_t ring_cap;
   RunCounters *ctr;
-  int32_t rule_kind;
-  int64_t rule_num, rule_den;
-  int32_t min_size;
-  uint64_t wait_limit_ns;
+  uint64_t wait_limit_ns;     // longest wait for a published item while work is pending
+  uint64_t idle_limit_ns;     // open kernels leave after this long with nothing pending
   // per-CTA global working memory for items that do not fit in shared memory
   char *slab;
   size_t slab_bytes;          // per CTA
@@ -136,5 +155,47 @@ size_t refine_smem_max_bytes(int device);
 // smem_bytes of dynamic shared memory each.
 int refine_max_ctas(int device, size_t smem_bytes);
 void launch_refine(const RefineParams &p, int grid, bool cooperative, cudaStream_t s);
+
+// ---- pipeline.cu: the stages around the refinement kernel ------------------
+// Result of grouping one request's vertices by input label.
+struct GroupInfo {
+  int64_t clusters;   // distinct labels >= 0
+  int64_t skip;       // unclustered vertices
+  int64_t kept;       // clusters with >= min_size vertices (they become items)
+  int64_t max_n;      // largest kept cluster
+  int64_t max_dsum;   // largest degree sum of a kept cluster
+};
+
+// a2: groups the vertices of labels (device) by input label (stable radix
+// sort), computes the kept clusters, their sizes and degree sums, and orders
+// them largest first.  Leaves its arrays in ws for seed_items().  One
+// read-back inside (the sort width) plus one at the end (the result).
+GroupInfo group_by_label(const int64_t *off, int64_t n, const int32_t *labels, int min_size,
+                         Workspace &ws, cudaStream_t s);
+
+// Publishes the kept clusters of the last group_by_label() on ws as ITEM_TOP
+// items of request `req` (context at reqs_dev + req): reserves their queue
+// indices, fills pool and slot (which must hold ~0 for every vertex), writes
+// the descriptors and publishes them.  Asynchronous on s.
+void seed_items(const GroupInfo &gi, int64_t n, Workspace &ws, uint16_t req, ReqCtx *ctx_dev,
+                int32_t *pool, unsigned long long *slot, QSlot *ring, uint64_t cap,
+                RunCounters *ctr, cudaStream_t s);
+
+// a9: out[v] = rank of the accepted cluster whose smallest vertex is
+// label_min[v] (ascending), -1 where label_min is -1.  Asynchronous on s.
+void number_clusters(const int32_t *label_min, int64_t n, int32_t *out, Workspace &ws,
+                     cudaStream_t s);
+
+int64_t bitlen_u64(uint64_t x);
+unsigned grid_for(int64_t n, int per = 256);
+void check_device_error(unsigned err, const char *what);
+
+template <typename T>
+T read_back(const T *dev, cudaStream_t s) {
+  T h;
+  WCC_CUDA(cudaMemcpyAsync(&h, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
 
 }  // namespace wccg

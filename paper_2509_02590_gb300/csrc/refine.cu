@@ -395,8 +395,9 @@ __device__ __forceinline__ int components_af(const Mem<IT> &m, int n, int32_t *f
 // with at least min_size members becomes a new queue item whose vertex list
 // (ascending) is written into the parent's pool range.  Uses C, D, E, F.
 template <typename IT>
-__device__ __forceinline__ void emit_children(const RefineParams &P, const Mem<IT> &m, const int32_t *tag, int n,
-                              int64_t vbeg, Sh &sh) {
+__device__ __forceinline__ void emit_children(const RefineParams &P, ReqCtx &R, uint16_t req,
+                                              const Mem<IT> &m, const int32_t *tag, int n,
+                                              int64_t vbeg, Sh &sh) {
   int32_t *cnt = m.C, *cidx = m.D, *cbase = m.E, *run = m.F;
   for (int t = threadIdx.x; t < n; t += RB) cnt[t] = 0;
   __syncthreads();
@@ -404,7 +405,7 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const Mem<I
     if (tag[i] >= 0) atomicAdd(&cnt[tag[i]], 1);
   __syncthreads();
   for (int t = threadIdx.x; t < n; t += RB) {
-    bool keep = cnt[t] >= P.min_size;
+    bool keep = cnt[t] >= R.min_size;
     cidx[t] = keep ? 1 : 0;
     cbase[t] = keep ? cnt[t] : 0;
     run[t] = 0;
@@ -414,8 +415,10 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const Mem<I
   block_scan_array(cbase, n, sh);
   if (nchild == 0) return;
   if (threadIdx.x == 0) {
-    sh.u0 = atomicAdd(&P.ctr->tail, (unsigned long long)nchild);
+    add_ll(&R.pending, (long long)nchild);
     add_ll(&P.ctr->pending, (long long)nchild);
+    __threadfence();
+    sh.u0 = atomicAdd(&P.ctr->tail, (unsigned long long)nchild);
   }
   __syncthreads();
   const unsigned long long s0 = sh.u0;
@@ -425,7 +428,7 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const Mem<I
     for (int b = 0; b < n; b += 32) {
       int i = b + lane;
       int t = i < n ? tag[i] : -1;
-      bool kept = t >= 0 && cnt[t] >= P.min_size;
+      bool kept = t >= 0 && cnt[t] >= R.min_size;
       int key = kept ? t : -1;
       unsigned peers = __match_any_sync(FULL, key);
       int rank = __popc(peers & lanemask_lt());
@@ -434,8 +437,8 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const Mem<I
       if (kept) {
         int pos = before + rank;
         int32_t v = m.gid[i];
-        P.pool[vbeg + cbase[t] + pos] = v;
-        P.slot[v] = ((unsigned long long)(s0 + cidx[t]) << 32) | (unsigned)pos;
+        R.pool[vbeg + cbase[t] + pos] = v;
+        R.slot[v] = ((unsigned long long)(s0 + cidx[t]) << 32) | (unsigned)pos;
         if (rank == 0) run[t] = before + __popc(peers);
       }
       __syncwarp();
@@ -445,17 +448,18 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const Mem<I
   __threadfence();
   // descriptors, then publication
   for (int t = threadIdx.x; t < n; t += RB) {
-    if (cnt[t] < P.min_size) continue;
+    if (cnt[t] < R.min_size) continue;
     unsigned long long q = s0 + cidx[t];
     QSlot *sl = &P.ring[q % P.ring_cap];
     sl->item.vbeg = vbeg + cbase[t];
     sl->item.n = cnt[t];
     sl->item.flags = 0;
+    sl->item.req = req;
   }
   __threadfence();
   __syncthreads();
   for (int t = threadIdx.x; t < n; t += RB) {
-    if (cnt[t] < P.min_size) continue;
+    if (cnt[t] < R.min_size) continue;
     unsigned long long q = s0 + cidx[t];
     atomicExch((unsigned long long *)&P.ring[q % P.ring_cap].seq, q);
   }
@@ -868,18 +872,19 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   const int n = it.n;
   const int64_t vbeg = it.vbeg;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  RunCounters *ctr = P.ctr;
+  ReqCtx &R = P.reqs[it.req];
+  ReqCtx *ctr = &R;  // per-request statistics
   Mem<IT> m = carve<IT>(base, n, dbound);
 
   // global row start and degree of every member
   int64_t *gbeg = m.wide;
   int32_t *pdeg = m.C, *cnt = m.D;
   for (int i = threadIdx.x; i < n; i += RB) {
-    const int32_t v = P.pool[vbeg + i];
+    const int32_t v = __ldcg(&R.pool[vbeg + i]);
     m.gid[i] = v;
-    const int64_t b = P.off[v];
+    const int64_t b = R.off[v];
     gbeg[i] = b;
-    pdeg[i] = (int32_t)(P.off[v + 1] - b);
+    pdeg[i] = (int32_t)(R.off[v + 1] - b);
     cnt[i] = 0;
   }
   __syncthreads();
@@ -917,12 +922,12 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
         if (f < f1) {
           while (pdeg[row + 1] <= f) ++row;
           rs[k] = row;
-          us[k] = P.adj[gbeg[row] + (f - pdeg[row])];
+          us[k] = R.adj[gbeg[row] + (f - pdeg[row])];
         }
       }
       unsigned long long sl[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) sl[k] = fs[k] < f1 ? P.slot[us[k]] : 0ull;
+      for (int k = 0; k < 4; ++k) sl[k] = fs[k] < f1 ? __ldcg(&R.slot[us[k]]) : 0ull;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (fs[k] >= f1) continue;
@@ -975,7 +980,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (it.flags & ITEM_TOP) {
     int nc = components_af(m, n, m.B, m.H, sh);
     if (nc != 1) {
-      emit_children(P, m, m.B, n, vbeg, sh);
+      emit_children(P, R, it.req, m, m.B, n, vbeg, sh);
       return OUT_CCR_SPLIT;
     }
   }
@@ -987,7 +992,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   __syncthreads();
   int nalive = n;
   for (;;) {
-    const int64_t T = threshold_of(P.rule_kind, P.rule_num, P.rule_den, nalive);
+    const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, nalive);
     int rem = 0;
     for (int i = threadIdx.x; i < n; i += RB) {
       bool r = m.alive[i] && deg[i] <= T;
@@ -1009,7 +1014,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
     sh.pf_nalive = nalive;
   }
   prof_stamp(P, sh, 4);
-  if (nalive < P.min_size) return OUT_DROPPED;
+  if (nalive < R.min_size) return OUT_DROPPED;
 
   // 4. connectivity of what is left (an item arrives connected: input
   // clusters passed CCR above, children are components or sides of a
@@ -1017,14 +1022,14 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (nalive < n) {
     int nc = components_af(m, n, m.B, m.H, sh);
     if (nc > 1) {
-      emit_children(P, m, m.B, n, vbeg, sh);
+      emit_children(P, R, it.req, m, m.B, n, vbeg, sh);
       return OUT_CC_SPLIT;
     }
   }
   prof_stamp(P, sh, 5);
 
   // 5. contraction with k = T+1
-  const int64_t T = threshold_of(P.rule_kind, P.rule_num, P.rule_den, nalive);
+  const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, nalive);
   const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
   int32_t *rep = m.A, *nrep = m.B;
   int nsv = 1, passes = 0;
@@ -1035,7 +1040,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
     if (bucketed) {
       if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
       ++passes;
-      const bool any = ma_pass_first(P, m, nrep, n, nalive, kcap, E, &ctr->error, sh);
+      const bool any = ma_pass_first(P, m, nrep, n, nalive, kcap, E, &P.ctr->error, sh);
       for (int i = threadIdx.x; i < n; i += RB) rep[i] = m.alive[i] ? (any ? nrep[i] : i) : -1;
       __syncthreads();
       more = any;
@@ -1052,7 +1057,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
       if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
       ++passes;
       if (bucketed)
-        ma_pass_bucketed(m, rep, nrep, n, nsv, kcap, &ctr->error, sh);
+        ma_pass_bucketed(m, rep, nrep, n, nsv, kcap, &P.ctr->error, sh);
       else
         ma_ordering(m, rep, nrep, nsv, kcap, sh);
       if (!sh.contracted) break;
@@ -1075,7 +1080,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
     __syncthreads();
     const int32_t minv = m.gid[sh.i0];
     for (int i = threadIdx.x; i < n; i += RB)
-      if (m.alive[i]) P.label_min[m.gid[i]] = minv;
+      if (m.alive[i]) R.label_min[m.gid[i]] = minv;
     if (threadIdx.x == 0) add_ll(&ctr->accepted, 1ll);
     __syncthreads();
     return OUT_ACCEPT;
@@ -1104,14 +1109,14 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
     }
     prof_stamp(P, sh, 7);
     if (best > T) {
-      if (threadIdx.x == 0) atomicOr(&ctr->error, DERR_INTERNAL);
+      if (threadIdx.x == 0) atomicOr(&P.ctr->error, DERR_INTERNAL);
       return OUT_ERROR;
     }
   }
   if (threadIdx.x == 0) add_ll(&ctr->splits, 1ll);
   for (int i = threadIdx.x; i < n; i += RB) m.B[i] = m.alive[i] ? (m.side[i] ? 1 : 0) : -1;
   __syncthreads();
-  emit_children(P, m, m.B, n, vbeg, sh);
+  emit_children(P, R, it.req, m, m.B, n, vbeg, sh);
   return OUT_CUT_SPLIT;
 }
 
@@ -1120,10 +1125,11 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
 __device__ int run_item(const RefineParams &P, unsigned long long seq, const Item &it, char *slab,
                         Sh &sh) {
   const int n = it.n;
+  const ReqCtx &R = P.reqs[it.req];
   long long dsum = 0;
   for (int i = threadIdx.x; i < n; i += RB) {
-    const int32_t v = P.pool[it.vbeg + i];
-    dsum += P.off[v + 1] - P.off[v];
+    const int32_t v = __ldcg(&R.pool[it.vbeg + i]);
+    dsum += R.off[v + 1] - R.off[v];
   }
   dsum = block_sum_ll(dsum, sh);
   const bool narrow = n < 65535;
@@ -1145,42 +1151,74 @@ __device__ int run_item(const RefineParams &P, unsigned long long seq, const Ite
 }
 
 // ---- the persistent kernel ---------------------------------------------------
+// Thread 0 claims a queue index only when one has been reserved (head <
+// tail), by compare-and-swap, and then waits -- bounded by wait_limit_ns --
+// for its publication.  With nothing reserved it waits for more: the kernel
+// ends when nothing is pending and the queue is closed, or (open, serving)
+// when nothing has been pending for idle_limit_ns; a wait for work that is
+// pending but never published ends at wait_limit_ns with DERR_TIMEOUT.
 __global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
   __shared__ Sh sh;
   char *slab = P.slab + (size_t)blockIdx.x * P.slab_bytes;
   RunCounters *ctr = P.ctr;
+  volatile RunCounters *vctr = ctr;
   for (;;) {
     if (threadIdx.x == 0) {
-      int go = 1;
-      unsigned long long j;
-      if (P.single_item) {
-        j = P.single_index;
-      } else {
-        j = atomicAdd(&ctr->head, 1ull);
-      }
-      QSlot *sl = &P.ring[j % P.ring_cap];
+      int go = 0;
+      unsigned long long j = 0;
       const uint64_t t0 = globaltimer_ns();
       unsigned ns = 32;
       for (;;) {
-        unsigned long long s = *(volatile unsigned long long *)&sl->seq;
-        if (s == j) break;
-        if (*(volatile unsigned *)&ctr->error != 0) { go = 0; break; }
-        if (*(volatile long long *)&ctr->pending <= 0) { go = 0; break; }
-        if (globaltimer_ns() - t0 > P.wait_limit_ns) {
+        if (vctr->error != 0) break;
+        if (P.single_item) {
+          j = P.single_index;
+          go = 1;
+          break;
+        }
+        const unsigned long long h = vctr->head, t = vctr->tail;
+        if (h < t) {
+          if (atomicCAS(&ctr->head, h, h + 1) == h) {
+            j = h;
+            go = 1;
+            break;
+          }
+          continue;
+        }
+        const long long pend = vctr->pending;
+        const uint64_t waited = globaltimer_ns() - t0;
+        if (pend <= 0) {
+          if (!vctr->open || waited > P.idle_limit_ns) break;
+        } else if (waited > P.wait_limit_ns) {
           atomicOr(&ctr->error, DERR_TIMEOUT);
-          go = 0;
           break;
         }
         __nanosleep(ns);
         ns = ns < 4096 ? ns * 2 : ns;
       }
-      __threadfence();
       if (go) {
-        volatile Item *vi = &sl->item;
-        sh.item.vbeg = vi->vbeg;
-        sh.item.n = vi->n;
-        sh.item.flags = vi->flags;
-        sh.seq = j;
+        // the claimed index is reserved; wait for its publication
+        QSlot *sl = &P.ring[j % P.ring_cap];
+        const uint64_t t1 = globaltimer_ns();
+        unsigned ns2 = 32;
+        for (;;) {
+          if (*(volatile unsigned long long *)&sl->seq == j) break;
+          if (vctr->error != 0 || globaltimer_ns() - t1 > P.wait_limit_ns) {
+            atomicOr(&ctr->error, DERR_TIMEOUT);
+            go = 0;
+            break;
+          }
+          __nanosleep(ns2);
+          ns2 = ns2 < 1024 ? ns2 * 2 : ns2;
+        }
+        __threadfence();
+        if (go) {
+          volatile Item *vi = &sl->item;
+          sh.item.vbeg = vi->vbeg;
+          sh.item.n = vi->n;
+          sh.item.flags = vi->flags;
+          sh.item.req = vi->req;
+          sh.seq = j;
+        }
       }
       sh.go = go;
     }
@@ -1224,6 +1262,14 @@ __global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
     }
     if (threadIdx.x == 0) {
       __threadfence();
+      ReqCtx &R = P.reqs[it.req];
+      const unsigned long long left =
+          atomicAdd(reinterpret_cast<unsigned long long *>(&R.pending), ~0ull);  // -1
+      if (left == 1ull && P.done_flags) {
+        // the request's last item: everything it wrote is visible first
+        __threadfence_system();
+        ((volatile int *)P.done_flags)[it.req] = 1;
+      }
       add_ll(&ctr->pending, -1ll);
     }
     if (P.single_item) break;
