@@ -145,6 +145,45 @@ int wcc_run(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshol
 /* Release a graph (NULL is ignored). */
 void wcc_destroy_graph(wcc_graph *g);
 
+/* ---- serving: continuous batching of refinement requests ----------------
+ * A server refines many requests at once in one persistent kernel: requests
+ * are admitted in arrival order whenever a request slot is free and their
+ * estimated device memory fits the budget, and a request admitted while
+ * others are on the GPU joins the running kernel at once (its work overlaps
+ * theirs).  Every result equals what wcc_run returns for the same input.
+ * The server takes the device current at wcc_server_create; every graph
+ * submitted must live on that device and stay alive (not destroyed) until
+ * its request has been collected by wcc_poll / wcc_wait. */
+
+/* Create a server using at most mem_budget_bytes of device memory for its
+ * queue, slabs and admitted requests.  WCC_ERR_INVALID if the budget cannot
+ * hold the fixed structures and one small request. */
+int wcc_server_create(int64_t mem_budget_bytes, wcc_server **out);
+
+/* Queue a refinement of graph g with the host clustering clustering_in[n]
+ * (copied before the call returns), rule (NULL = LOG10) and min_size as in
+ * wcc_run.  *ticket identifies the request.  WCC_ERR_BUSY when the request
+ * can never fit the server's budget or queue. */
+int wcc_submit(wcc_server *s, const wcc_graph *g, const int32_t *clustering_in,
+               const wcc_threshold_rule *rule, int32_t min_size, uint64_t *ticket);
+
+/* Non-blocking: WCC_PENDING while the request runs; WCC_OK once finished,
+ * with the result written to the host buffer clustering_out[n] (numbered as
+ * in wcc_run) and stats filled (nullable; ms_total = submit to finish,
+ * ms_refine = admission to finish, ms_membership = grouping); or the
+ * request's error.  A ticket is collected once; afterwards it is unknown
+ * (WCC_ERR_INVALID). */
+int wcc_poll(wcc_server *s, uint64_t ticket, int32_t *clustering_out, wcc_stats *stats);
+
+/* As wcc_poll, but waits up to timeout_ms for the request to finish;
+ * returns WCC_PENDING if it is still running then. */
+int wcc_wait(wcc_server *s, uint64_t ticket, int64_t timeout_ms, int32_t *clustering_out,
+             wcc_stats *stats);
+
+/* Finish every submitted request, stop the server and release it (NULL is
+ * ignored).  Results not collected by then are discarded. */
+void wcc_server_destroy(wcc_server *s);
+
 /* Build a CSR without allocating any memory.  The paper has no counterpart:
  * this is a service for callers that cannot allocate device memory, for
  * example code running under an allocator that owns the whole device, a

@@ -17,7 +17,8 @@ from ._binding import (WCC_MODE_BATCHED, WCC_MODE_PLAIN, WCC_RULE_LINEAR,  # noq
                        wcc_build_csr_no_alloc, wcc_create_graph,
                        wcc_create_graph_from_edges, wcc_destroy_graph, wcc_graph_export_csr,
                        wcc_graph_nnz, wcc_graph_num_vertices, wcc_kernel_launches,
-                       wcc_last_error, wcc_run,
+                       wcc_last_error, wcc_poll, wcc_run, wcc_server_create,
+                       wcc_server_destroy, wcc_submit, wcc_wait,
                        wcc_stats, wcc_threshold_rule)
 
 _RULES = {"log10": WCC_RULE_LOG10, "log2": WCC_RULE_LOG2, "sqrt": WCC_RULE_SQRT,
@@ -126,8 +127,69 @@ class WccGraph:
             pass
 
 
-__all__ = ["WccGraph", "WccError", "rule_struct", "wcc_create_graph",
+class WccServer:
+    """A continuous-batching refinement server (owns a ``wcc_server``).
+
+    Requests carry host (numpy) clusterings; results come back as numpy
+    arrays.  A graph must stay open until its requests are collected."""
+
+    def __init__(self, mem_budget_bytes: int):
+        self.handle = wcc_server_create(int(mem_budget_bytes))
+        self._n = {}
+
+    def submit(self, graph: WccGraph, labels, min_size: int = 2, rule="log10", num: int = 1,
+               den: int = 1) -> int:
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        if len(lab) != graph.n:
+            raise ValueError("labels must have one entry per vertex")
+        t = wcc_submit(self.handle, graph.handle, lab.ctypes.data, rule_struct(rule, num, den),
+                       min_size)
+        self._n[t] = graph.n
+        return t
+
+    def _collect(self, fn, ticket, *args):
+        n = self._n[ticket]
+        out = np.empty(max(n, 1), np.int32)
+        st = wcc_stats()
+        try:
+            r = fn(self.handle, ticket, *args, out.ctypes.data, st)
+        except WccError:
+            self._n.pop(ticket, None)
+            raise
+        if r != _binding.WCC_OK:
+            return None
+        self._n.pop(ticket, None)
+        return out[:n], st.as_dict()
+
+    def poll(self, ticket: int):
+        """(labels, stats) when finished, else None."""
+        return self._collect(wcc_poll, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = 600_000):
+        """(labels, stats) once finished, or None after timeout_ms."""
+        return self._collect(wcc_wait, ticket, int(timeout_ms))
+
+    def close(self):
+        if self.handle:
+            wcc_server_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ = ["WccServer", "WccGraph", "WccError", "rule_struct", "wcc_create_graph",
            "wcc_create_graph_from_edges", "wcc_run", "wcc_destroy_graph", "wcc_last_error",
            "wcc_graph_num_vertices", "wcc_graph_nnz", "wcc_kernel_launches", "wcc_build_csr_no_alloc", "wcc_graph_export_csr", "wcc_stats",
-           "wcc_threshold_rule", "WCC_MODE_BATCHED", "WCC_MODE_PLAIN"]
+           "wcc_threshold_rule", "WCC_MODE_BATCHED", "WCC_MODE_PLAIN", "wcc_server_create",
+           "wcc_submit", "wcc_poll", "wcc_wait", "wcc_server_destroy"]
 _ = ctypes

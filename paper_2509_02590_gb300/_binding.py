@@ -74,6 +74,17 @@ def _load():
     L.wcc_run.restype = c_int
     L.wcc_destroy_graph.argtypes = [vp]
     L.wcc_destroy_graph.restype = None
+    L.wcc_server_create.argtypes = [i64, gpp]
+    L.wcc_server_create.restype = c_int
+    L.wcc_submit.argtypes = [vp, vp, vp, ctypes.POINTER(wcc_threshold_rule), i32,
+                             ctypes.POINTER(ctypes.c_uint64)]
+    L.wcc_submit.restype = c_int
+    L.wcc_poll.argtypes = [vp, ctypes.c_uint64, vp, ctypes.POINTER(wcc_stats)]
+    L.wcc_poll.restype = c_int
+    L.wcc_wait.argtypes = [vp, ctypes.c_uint64, i64, vp, ctypes.POINTER(wcc_stats)]
+    L.wcc_wait.restype = c_int
+    L.wcc_server_destroy.argtypes = [vp]
+    L.wcc_server_destroy.restype = None
     L.wcc_build_csr_no_alloc.argtypes = [vp, vp, i64, i64, vp, vp, ctypes.POINTER(i64), vp]
     L.wcc_build_csr_no_alloc.restype = c_int
     L.wcc_kernel_launches.argtypes = []
@@ -84,6 +95,39 @@ def _load():
 
 
 lib = _load()
+
+
+def wcc_server_create(mem_budget_bytes: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.wcc_server_create(mem_budget_bytes, ctypes.byref(out)))
+    return out.value
+
+
+def wcc_submit(server: int, g: int, clustering_in: int, rule: wcc_threshold_rule | None,
+               min_size: int) -> int:
+    t = ctypes.c_uint64(0)
+    _check(lib.wcc_submit(server, g, clustering_in,
+                          ctypes.byref(rule) if rule is not None else None, min_size,
+                          ctypes.byref(t)))
+    return int(t.value)
+
+
+def wcc_poll(server: int, ticket: int, clustering_out: int,
+             stats: wcc_stats | None = None) -> int:
+    """WCC_OK or WCC_PENDING (raises on the request's error)."""
+    return _check(lib.wcc_poll(server, ticket, clustering_out,
+                               ctypes.byref(stats) if stats is not None else None))
+
+
+def wcc_wait(server: int, ticket: int, timeout_ms: int, clustering_out: int,
+             stats: wcc_stats | None = None) -> int:
+    """WCC_OK or WCC_PENDING after timeout_ms (raises on the request's error)."""
+    return _check(lib.wcc_wait(server, ticket, timeout_ms, clustering_out,
+                               ctypes.byref(stats) if stats is not None else None))
+
+
+def wcc_server_destroy(server: int) -> None:
+    lib.wcc_server_destroy(server)
 
 
 def wcc_build_csr_no_alloc(src: int, dst: int, m: int, n: int, row_off: int, cols: int,

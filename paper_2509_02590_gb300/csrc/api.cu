@@ -17,6 +17,8 @@ static thread_local std::string g_last_error;
 
 void fail(int code, const std::string &msg) { throw Error{code, msg}; }
 
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
 static std::atomic<int64_t> g_launches{0};
 void note_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
@@ -98,6 +100,52 @@ void *DevBuf::ensure(size_t b) {
   }
   bytes = want;
   return p;
+}
+
+int current_device() {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    (void)cudaGetLastError();
+    fail(WCC_ERR_CUDA, std::string("no usable CUDA device: ") +
+                           (e != cudaSuccess ? cudaGetErrorString(e) : "device count is 0"));
+  }
+  int dev = 0;
+  WCC_CUDA(cudaGetDevice(&dev));
+  return dev;
+}
+
+// Limit of every device-side queue wait (WCC_WAIT_LIMIT_MS, default 30 s):
+// a CTA that waits longer sets DERR_TIMEOUT and leaves, so a fault in the
+// queue protocol ends the kernel instead of hanging the GPU.
+uint64_t wait_limit_ns() {
+  const char *e = getenv("WCC_WAIT_LIMIT_MS");
+  long long ms = e ? atoll(e) : 30000;
+  if (ms < 1) ms = 1;
+  return (uint64_t)ms * 1000000ull;
+}
+
+// Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
+// largest a CTA can opt into, one CTA per SM).  Items whose working set is
+// larger use a global slab.
+size_t refine_smem_bytes_config(int device) {
+  const char *e = getenv("WCC_SMEM_KB");
+  long long kb = e ? atoll(e) : (1ll << 30);
+  long long mx = (long long)(refine_smem_max_bytes(device) / 1024);
+  if (kb < 16) kb = 16;
+  if (kb > mx) kb = mx;
+  return (size_t)kb * 1024;
+}
+
+// Validates a threshold rule and min_size; returns the rule to use.
+wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule) {
+  wcc_threshold_rule r = rule ? *rule : wcc_threshold_rule{WCC_RULE_LOG10, 0, 0, 1};
+  if (r.kind < WCC_RULE_LOG10 || r.kind > WCC_RULE_LINEAR)
+    fail(WCC_ERR_INVALID, "unknown threshold rule kind " + std::to_string(r.kind));
+  if (r.kind == WCC_RULE_LINEAR &&
+      (r.den <= 0 || r.num < 0 || r.den >= (1ll << 31) || r.num >= (1ll << 31)))
+    fail(WCC_ERR_INVALID, "LINEAR rule needs 0 <= num < 2^31 and 0 < den < 2^31");
+  return r;
 }
 
 namespace {
@@ -192,42 +240,10 @@ struct DeviceGuard {
   }
 };
 
-int current_device() {
-  int count = 0;
-  cudaError_t e = cudaGetDeviceCount(&count);
-  if (e != cudaSuccess || count == 0) {
-    (void)cudaGetLastError();
-    fail(WCC_ERR_CUDA, std::string("no usable CUDA device: ") +
-                           (e != cudaSuccess ? cudaGetErrorString(e) : "device count is 0"));
-  }
-  int dev = 0;
-  WCC_CUDA(cudaGetDevice(&dev));
-  return dev;
-}
 
 void check_derr(unsigned err, const char *what) { check_device_error(err, what); }
 
-// Limit of every device-side queue wait (WCC_WAIT_LIMIT_MS, default 30 s):
-// a CTA that waits longer sets DERR_TIMEOUT and leaves, so a fault in the
-// queue protocol ends the kernel instead of hanging the GPU.
-uint64_t wait_limit_ns() {
-  const char *e = getenv("WCC_WAIT_LIMIT_MS");
-  long long ms = e ? atoll(e) : 30000;
-  if (ms < 1) ms = 1;
-  return (uint64_t)ms * 1000000ull;
-}
 
-// Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
-// largest a CTA can opt into, one CTA per SM).  Items whose working set is
-// larger use a global slab.
-size_t refine_smem_bytes_config(int device) {
-  const char *e = getenv("WCC_SMEM_KB");
-  long long kb = e ? atoll(e) : (1ll << 30);
-  long long mx = (long long)(refine_smem_max_bytes(device) / 1024);
-  if (kb < 16) kb = 16;
-  if (kb > mx) kb = mx;
-  return (size_t)kb * 1024;
-}
 
 
 // Writes the per-item profile of the last refinement as CSV (appending).
@@ -275,16 +291,6 @@ struct Timer {
   }
 };
 
-// Validates a threshold rule and min_size; returns the rule to use.
-wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule) {
-  wcc_threshold_rule r = rule ? *rule : wcc_threshold_rule{WCC_RULE_LOG10, 0, 0, 1};
-  if (r.kind < WCC_RULE_LOG10 || r.kind > WCC_RULE_LINEAR)
-    fail(WCC_ERR_INVALID, "unknown threshold rule kind " + std::to_string(r.kind));
-  if (r.kind == WCC_RULE_LINEAR &&
-      (r.den <= 0 || r.num < 0 || r.den >= (1ll << 31) || r.num >= (1ll << 31)))
-    fail(WCC_ERR_INVALID, "LINEAR rule needs 0 <= num < 2^31 and 0 < den < 2^31");
-  return r;
-}
 
 enum RunBuf { R_IN, R_OUT, R_POOL, R_SLOT, R_LMIN, R_RING, R_CTR, R_SLAB, R_REQ, R_COUNT };
 static_assert(R_COUNT <= 16, "run buffers");
@@ -626,9 +632,6 @@ int guarded(F &&f) {
 }  // namespace
 }  // namespace wccg
 
-struct wcc_graph {
-  wccg::Graph *g;
-};
 
 using namespace wccg;
 

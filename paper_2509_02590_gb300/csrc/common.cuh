@@ -19,6 +19,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const std::string &msg);
+void set_last_error(const std::string &msg);  // the thread-local message of wcc_last_error()
 
 #define WCC_CUDA(call)                                                               \
   do {                                                                               \
@@ -38,6 +39,13 @@ enum : uint32_t {
 };
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// The 32-bit tag a vertex's slot holds for the queue index of its current
+// item.  Never all ones (the "no item" value), and unique among any 2^32-1
+// consecutive indices, which outlive every request.
+__host__ __device__ __forceinline__ uint32_t queue_tag(unsigned long long q) {
+  return (uint32_t)(q % 0xffffffffull);
+}
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;

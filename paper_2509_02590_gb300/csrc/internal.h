@@ -190,6 +190,12 @@ int64_t bitlen_u64(uint64_t x);
 unsigned grid_for(int64_t n, int per = 256);
 void check_device_error(unsigned err, const char *what);
 
+// ---- api.cu helpers shared with the server ------------------------------------
+int current_device();                       // fails with WCC_ERR_CUDA without a GPU
+uint64_t wait_limit_ns();                   // WCC_WAIT_LIMIT_MS (default 30 s)
+size_t refine_smem_bytes_config(int device);  // WCC_SMEM_KB (default: opt-in maximum)
+wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule);
+
 template <typename T>
 T read_back(const T *dev, cudaStream_t s) {
   T h;
@@ -199,3 +205,8 @@ T read_back(const T *dev, cudaStream_t s) {
 }
 
 }  // namespace wccg
+
+// The opaque handle of the C ABI.
+struct wcc_graph {
+  wccg::Graph *g;
+};

@@ -142,7 +142,7 @@ __global__ void k_pool_slots(const uint32_t *__restrict__ sv, const uint32_t *__
   pool[i - skip] = (int32_t)v;
   int64_t c = (int64_t)hidx[i] + head[i] - 1;  // inclusive head count - 1
   if (keep[c])
-    slot[v] = ((unsigned long long)(*base + qidx[c]) << 32) | (unsigned)(i - cstart[c]);
+    slot[v] = ((unsigned long long)queue_tag(*base + qidx[c]) << 32) | (unsigned)(i - cstart[c]);
 }
 
 // Descriptors of the kept clusters, then their publication.

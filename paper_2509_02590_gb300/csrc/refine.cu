@@ -144,6 +144,25 @@ __device__ __forceinline__ void prof_stamp(const RefineParams &P, Sh &sh, int k)
 
 // ---- small device helpers ----------------------------------------------------
 
+// A request's context as this CTA sees it: loaded through L2 (not L1), since
+// a server reuses a table entry for a later request while the kernel runs.
+__device__ __forceinline__ ReqCtx load_ctx(const ReqCtx *g) {
+  ReqCtx r;
+  r.off = reinterpret_cast<const int64_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&g->off)));
+  r.adj = reinterpret_cast<const int32_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&g->adj)));
+  r.n_vertices = __ldcg(reinterpret_cast<const long long *>(&g->n_vertices));
+  r.pool = reinterpret_cast<int32_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&g->pool)));
+  r.slot = reinterpret_cast<unsigned long long *>(
+      __ldcg(reinterpret_cast<const unsigned long long *>(&g->slot)));
+  r.label_min =
+      reinterpret_cast<int32_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&g->label_min)));
+  r.rule_kind = __ldcg(&g->rule_kind);
+  r.min_size = __ldcg(&g->min_size);
+  r.rule_num = __ldcg(reinterpret_cast<const long long *>(&g->rule_num));
+  r.rule_den = __ldcg(reinterpret_cast<const long long *>(&g->rule_den));
+  return r;
+}
+
 // Signed 64-bit atomic add (two's complement through the unsigned overload).
 __device__ __forceinline__ void add_ll(long long *p, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
@@ -395,9 +414,9 @@ __device__ __forceinline__ int components_af(const Mem<IT> &m, int n, int32_t *f
 // with at least min_size members becomes a new queue item whose vertex list
 // (ascending) is written into the parent's pool range.  Uses C, D, E, F.
 template <typename IT>
-__device__ __forceinline__ void emit_children(const RefineParams &P, ReqCtx &R, uint16_t req,
-                                              const Mem<IT> &m, const int32_t *tag, int n,
-                                              int64_t vbeg, Sh &sh) {
+__device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCtx &R,
+                                              ReqCtx *Rg, uint16_t req, const Mem<IT> &m,
+                                              const int32_t *tag, int n, int64_t vbeg, Sh &sh) {
   int32_t *cnt = m.C, *cidx = m.D, *cbase = m.E, *run = m.F;
   for (int t = threadIdx.x; t < n; t += RB) cnt[t] = 0;
   __syncthreads();
@@ -415,7 +434,7 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, ReqCtx &R, 
   block_scan_array(cbase, n, sh);
   if (nchild == 0) return;
   if (threadIdx.x == 0) {
-    add_ll(&R.pending, (long long)nchild);
+    add_ll(&Rg->pending, (long long)nchild);
     add_ll(&P.ctr->pending, (long long)nchild);
     __threadfence();
     sh.u0 = atomicAdd(&P.ctr->tail, (unsigned long long)nchild);
@@ -438,7 +457,7 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, ReqCtx &R, 
         int pos = before + rank;
         int32_t v = m.gid[i];
         R.pool[vbeg + cbase[t] + pos] = v;
-        R.slot[v] = ((unsigned long long)(s0 + cidx[t]) << 32) | (unsigned)pos;
+        R.slot[v] = ((unsigned long long)queue_tag(s0 + cidx[t]) << 32) | (unsigned)pos;
         if (rank == 0) run[t] = before + __popc(peers);
       }
       __syncwarp();
@@ -872,8 +891,9 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   const int n = it.n;
   const int64_t vbeg = it.vbeg;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  ReqCtx &R = P.reqs[it.req];
-  ReqCtx *ctr = &R;  // per-request statistics
+  ReqCtx *Rg = &P.reqs[it.req];
+  const ReqCtx R = load_ctx(Rg);
+  ReqCtx *ctr = Rg;  // per-request statistics (atomics)
   Mem<IT> m = carve<IT>(base, n, dbound);
 
   // global row start and degree of every member
@@ -931,7 +951,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (fs[k] >= f1) continue;
-        const bool hit = (unsigned)(sl[k] >> 32) == (unsigned)seq;
+        const bool hit = (unsigned)(sl[k] >> 32) == queue_tag(seq);
         tmp[fs[k]] = hit ? (IT)(unsigned)(sl[k] & 0xffffffffu) : NONE;
         if (hit) atomicAdd(&cnt[rs[k]], 1);
       }
@@ -980,7 +1000,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (it.flags & ITEM_TOP) {
     int nc = components_af(m, n, m.B, m.H, sh);
     if (nc != 1) {
-      emit_children(P, R, it.req, m, m.B, n, vbeg, sh);
+      emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh);
       return OUT_CCR_SPLIT;
     }
   }
@@ -1022,7 +1042,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (nalive < n) {
     int nc = components_af(m, n, m.B, m.H, sh);
     if (nc > 1) {
-      emit_children(P, R, it.req, m, m.B, n, vbeg, sh);
+      emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh);
       return OUT_CC_SPLIT;
     }
   }
@@ -1116,7 +1136,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (threadIdx.x == 0) add_ll(&ctr->splits, 1ll);
   for (int i = threadIdx.x; i < n; i += RB) m.B[i] = m.alive[i] ? (m.side[i] ? 1 : 0) : -1;
   __syncthreads();
-  emit_children(P, R, it.req, m, m.B, n, vbeg, sh);
+  emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh);
   return OUT_CUT_SPLIT;
 }
 
@@ -1125,7 +1145,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
 __device__ int run_item(const RefineParams &P, unsigned long long seq, const Item &it, char *slab,
                         Sh &sh) {
   const int n = it.n;
-  const ReqCtx &R = P.reqs[it.req];
+  const ReqCtx R = load_ctx(&P.reqs[it.req]);
   long long dsum = 0;
   for (int i = threadIdx.x; i < n; i += RB) {
     const int32_t v = __ldcg(&R.pool[it.vbeg + i]);
