@@ -184,6 +184,82 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ ranks
+def aggregate_ranks(dist, torch, dev, total_ms: float, m: int, clusters: int):
+    """Weak scaling across ranks: every rank refines its own instance with no
+    data-path collective; the job time is the slowest rank's and the work is
+    the sum over ranks.  Returns (max total_ms, sum of edges, sum of input
+    clusters).  dist may be None (one rank)."""
+    if dist is None:
+        return total_ms, float(m), float(clusters)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    mw = torch.tensor([float(m), float(clusters)], dtype=torch.float64, device=dev)
+    dist.all_reduce(mw)
+    return float(t.item()), float(mw[0].item()), float(mw[1].item())
+
+
+# ------------------------------------------------------------------ serving
+def serving_bench(wcc, np, torch, n_requests: int = 240, pool_size: int = 40, seed: int = 0):
+    """Serving sample of the request-stream workload: a pool of degree-
+    corrected planted-partition graphs with log-uniform edge counts in
+    [1e3, 1e7] (n = m/10, cluster sizes power law 1.5 on [20, 2000], degree
+    exponent 2.5), requests drawn uniformly from the pool.  Capacity is the
+    throughput of a burst of all requests; then the same number of requests
+    arrive as a Poisson process at 0.8 of that capacity and the latency of
+    each (submit to result, wcc_stats.ms_total) is recorded."""
+    import time as _t
+
+    from synth import gpu_graphs
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(pool_size):
+        m = int(10 ** rng.uniform(3, 7))
+        n = max(m // 10, 200)
+        w = gpu_graphs.dc_planted_gpu(n, m, seed=1000 + i, deg_exp=2.5, size_exp=1.5,
+                                      size_min=20, size_max=2000, f_in=0.8, chain_frac=0.05,
+                                      chain_parts=(2, 2))
+        g = wcc.WccGraph.from_edges(w.src, w.dst, w.n)
+        pool.append((g, w.labels.cpu().numpy(), w.m))
+        del w
+    picks = rng.integers(0, pool_size, n_requests)
+    edges = sum(pool[k][2] for k in picks)
+    with wcc.WccServer(80 << 30) as srv:
+        # capacity: everything at once
+        t0 = _t.perf_counter()
+        tickets = [srv.submit(pool[k][0], pool[k][1]) for k in picks]
+        for t in tickets:
+            srv.wait(t)
+        burst_s = _t.perf_counter() - t0
+        cap_rps = n_requests / burst_s
+        # Poisson arrivals at 0.8 of capacity
+        rate = 0.8 * cap_rps
+        gaps = rng.exponential(1.0 / rate, n_requests)
+        lat = []
+        tickets = []
+        t0 = _t.perf_counter()
+        nxt = t0
+        for k, gap in zip(picks, gaps):
+            nxt += gap
+            while _t.perf_counter() < nxt:
+                pass
+            tickets.append(srv.submit(pool[k][0], pool[k][1]))
+        for t in tickets:
+            _, st = srv.wait(t)
+            lat.append(st["ms_total"])
+        run_s = _t.perf_counter() - t0
+    for g, _, _ in pool:
+        g.close()
+    lat = sorted(lat)
+    return {"requests": n_requests, "edges": int(edges), "load": 0.8,
+            "capacity_requests_per_s": cap_rps, "capacity_edges_per_s": edges / burst_s,
+            "requests_per_s": n_requests / run_s, "edges_per_s": edges / run_s,
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1)) + 1)],
+            "mean_edges_per_request": edges / n_requests,
+            "sample": f"{n_requests} requests over a pool of {pool_size} graphs "
+                      "(log-uniform 1e3..1e7 edges), 80 GB budget"}
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -194,6 +270,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=240)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -262,16 +339,7 @@ def main():
     sampler.stop()
     clocks = sampler.summary(t_begin, t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        mw = torch.tensor([w.m, w.n_clusters], dtype=torch.float64, device=dev)
-        dist.all_reduce(mw)
-        m_all, k_all = float(mw[0].item()), float(mw[1].item())
-    else:
-        m_all, k_all = float(w.m), float(w.n_clusters)
+    total_ms, m_all, k_all = aggregate_ranks(dist, torch, dev, sum(step_ms), w.m, w.n_clusters)
     value = m_all * args.steps / (total_ms / 1e3)
     clusters_per_s = k_all * args.steps / (total_ms / 1e3)
     srt = sorted(step_ms)
@@ -332,6 +400,10 @@ def main():
         except (OSError, ValueError):
             pass
 
+    serving = None
+    if args.serving_requests > 0:
+        serving = serving_bench(wcc, np, torch, n_requests=args.serving_requests, seed=rank)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -345,7 +417,8 @@ def main():
                         "h2d_bytes_per_step": int(8 * w.m + 4 * w.n),
                         "d2h_bytes_per_step": int(4 * w.n), "ms_per_step": 1e3 * e2e_mean,
                         "matches_device_run": ok},
-                "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks}
+                "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
+                "serving": serving}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
