@@ -125,6 +125,17 @@ uint64_t wait_limit_ns() {
   return (uint64_t)ms * 1000000ull;
 }
 
+// Items of at least this many vertices first try the forest acceptance test
+// (WCC_FOREST_MIN_N; 0, the default, turns it off: on the measured workloads
+// the maximum-adjacency pass decides faster).
+int forest_min_n_config() {
+  const char *e = getenv("WCC_FOREST_MIN_N");
+  long long v = e ? atoll(e) : 0;
+  if (v < 0) v = 0;
+  if (v > (1ll << 30)) v = 1ll << 30;
+  return (int)v;
+}
+
 // Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
 // largest a CTA can opt into, one CTA per SM).  Items whose working set is
 // larger use a global slab.
@@ -258,12 +269,15 @@ void dump_item_profile(const RefineParams &p, const char *path, cudaStream_t s) 
   FILE *f = fopen(path, "a");
   if (!f) return;
   fprintf(f, "seq,n,E,nalive,passes,nsv,outcome,smid,slab,top,load,extract,ccr,peel,cc,contract,"
-             "sw,out,t_begin,p1_cycles,p1_pick,p1_steps,p1_scan\n");
+             "sw,out,t_begin,t_end,p1_cycles,p1_marks,p1_steps,later_passes,forest,nsv1,forest_cycles,f_bfs,f_levels,f_check,"
+             "f_trees,f_contract,f_relabel\n");
   for (const ItemProf &q : h)
-    fprintf(f, "%u,%d,%d,%d,%d,%d,%d,%d,%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%lld,%lld,%lld,%lld,%lld\n",
+    fprintf(f, "%u,%d,%d,%d,%d,%d,%d,%d,%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%lld,%lld,%lld,%lld,%lld,%lld,%d,%d,"
+               "%lld,%lld,%lld,%lld,%lld,%lld,%lld\n",
             q.seq, q.n, q.E, q.nalive, q.passes, q.nsv, q.outcome, q.smid, q.slab, q.top,
-            q.dt[0], q.dt[1], q.dt[2], q.dt[3], q.dt[4], q.dt[5], q.dt[6], q.dt[7], q.t_begin,
-            q.dbg[0], q.dbg[1], q.dbg[2], q.dbg[3]);
+            q.dt[0], q.dt[1], q.dt[2], q.dt[3], q.dt[4], q.dt[5], q.dt[6], q.dt[7], q.t_begin, q.t_end,
+            q.dbg[0], q.dbg[1], q.dbg[2], q.dbg[3], q.forest, q.nsv1, q.forest_cycles, q.fdbg[0],
+            q.fdbg[1], q.fdbg[2], q.fdbg[3], q.fdbg[4], q.fdbg[5]);
   fclose(f);
 }
 
@@ -368,6 +382,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     p.idle_limit_ns = 0;
     p.smem_bytes = smem_bytes;
     p.slab_bytes = slab_bytes;
+    p.forest_min_n = forest_min_n_config();
     // optional per-item profile (WCC_PROFILE_ITEMS=<csv path>)
     const char *prof_path = getenv("WCC_PROFILE_ITEMS");
     DevBuf prof_buf;

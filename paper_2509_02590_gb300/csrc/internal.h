@@ -123,8 +123,12 @@ struct ItemProf {
   unsigned seq;
   int n, E, nalive, passes, nsv, outcome, smid, slab, top;
   unsigned dt[8];
-  long long t_begin;
+  long long t_begin, t_end;  // %globaltimer (ns) when the item started and ended
   long long dbg[4];  // first contraction pass: loop cycles, pick cycles, steps, scan cycles
+  int forest;        // forest test: rounds it took (negative: gave up after that many)
+  int nsv1;          // super-vertices after the first contraction pass
+  long long forest_cycles;
+  long long fdbg[6];  // forest test: BFS cycles, BFS levels, tree checks, extra trees, degree+contraction, relabel
 };
 
 struct RefineParams {
@@ -139,6 +143,7 @@ struct RefineParams {
   char *slab;
   size_t slab_bytes;          // per CTA
   size_t smem_bytes;          // dynamic shared memory per CTA
+  int forest_min_n;           // smallest item that tries the forest acceptance test (0 = never)
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
   ItemProf *prof;             // optional per-item profile (NULL = off)
@@ -194,6 +199,7 @@ void check_device_error(unsigned err, const char *what);
 int current_device();                       // fails with WCC_ERR_CUDA without a GPU
 uint64_t wait_limit_ns();                   // WCC_WAIT_LIMIT_MS (default 30 s)
 size_t refine_smem_bytes_config(int device);  // WCC_SMEM_KB (default: opt-in maximum)
+int forest_min_n_config();                    // WCC_FOREST_MIN_N
 wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule);
 
 template <typename T>

@@ -126,11 +126,14 @@ struct Sh {
   int32_t ntouched;
   int32_t contracted;
   int32_t changed;
-  int32_t sw_s, sw_t, sw_cut;
+  int32_t sw_s, sw_t, sw_cut, sw_x, sw_key;
   // per-item profile (only when RefineParams::prof is set)
   long long ts[9];
   long long dbg[4];
-  int32_t used_slab, pf_E, pf_nalive, pf_passes, pf_nsv;
+  int32_t used_slab, pf_E, pf_nalive, pf_passes, pf_nsv, pf_forest, pf_nsv1;
+  long long pf_forest_cycles, pf_t0;
+  long long fdbg[6];
+  uint32_t sink[32];  // per-lane dummy targets of branch-free warp code
 };
 
 // Outcome of one item.
@@ -215,6 +218,19 @@ __device__ __forceinline__ void uf_union(int32_t *p, int a, int b) {
     int old = atomicCAS(&p[b], b, a);
     if (old == b) return;
     b = old;
+  }
+}
+
+// Like uf_union, but reports whether the call joined two different sets.
+// Concurrent calls are linearisable, so the edges whose call returned true
+// form a spanning forest of all the edges tried.
+__device__ __forceinline__ bool uf_link(int32_t *p, int a, int b) {
+  for (;;) {
+    a = uf_find(p, a);
+    b = uf_find(p, b);
+    if (a == b) return false;
+    if (a > b) { int t = a; a = b; b = t; }
+    if (atomicCAS(&p[b], b, a) == b) return true;
   }
 }
 
@@ -493,16 +509,31 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCt
 template <typename IT>
 __device__ __forceinline__ int group_members(const Mem<IT> &m, const int32_t *grp, int n, Sh &sh) {
   int32_t *gof = m.C, *mem = m.D, *svl = m.G, *tmp = m.H;
+  const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i <= n; i += RB) gof[i] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += RB)
-    if (m.alive[i]) atomicAdd(&gof[grp[i]], 1);
+  // counts and slots are taken once per group present in a warp (large
+  // super-vertices would otherwise serialise on one counter)
+  for (int base = 0; base < n; base += RB) {
+    const int i = base + threadIdx.x;
+    const int g = (i < n && m.alive[i]) ? grp[i] : -1;
+    const unsigned peers = __match_any_sync(FULL, g);
+    if (g >= 0 && lane == __ffs(peers) - 1) atomicAdd(&gof[g], __popc(peers));
+  }
   __syncthreads();
   block_scan_array(gof, n + 1, sh);
   for (int i = threadIdx.x; i < n; i += RB) tmp[i] = gof[i];
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += RB)
-    if (m.alive[i]) mem[atomicAdd(&tmp[grp[i]], 1)] = i;
+  for (int base = 0; base < n; base += RB) {
+    const int i = base + threadIdx.x;
+    const int g = (i < n && m.alive[i]) ? grp[i] : -1;
+    const unsigned peers = __match_any_sync(FULL, g);
+    const int leader = __ffs(peers) - 1;
+    int at = 0;
+    if (g >= 0 && lane == leader) at = atomicAdd(&tmp[g], __popc(peers));
+    at = __shfl_sync(FULL, at, leader);
+    if (g >= 0) mem[at + __popc(peers & lanemask_lt())] = i;
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += RB) tmp[i] = (m.alive[i] && grp[i] == i) ? 1 : 0;
   __syncthreads();
@@ -676,138 +707,338 @@ __device__ __forceinline__ void bucket_set(const Mem<IT> &m, int L, int Y) {
   atomicOr(&m.bms[L * m.S + (Y >> 10)], 1u << ((Y >> 5) & 31));
 }
 
+// Smallest id > p in level L of the cumulative key bitmaps that is not yet
+// added (vis), or -1; warp 0, all lanes.  Levels of more than 64 words are
+// searched through their summary bits; with clear set, summary bits whose
+// words hold no unadded member are cleared on the way (only when no key
+// update can run concurrently).
+__device__ __forceinline__ int next_member(volatile uint32_t *bm, volatile uint32_t *bms,
+                                           volatile uint32_t *vis, int W, int S, int L, int p,
+                                           bool clear) {
+  const int lane = threadIdx.x & 31;
+  const int p1 = p + 1, w1 = p1 >> 5;
+  const uint32_t first_mask = FULL << (p1 & 31);
+  if (W <= 64) {
+    uint32_t a = 0u, b = 0u;
+    if (lane < W && lane >= w1) a = bm[L * W + lane] & ~vis[lane];
+    if (lane + 32 < W && lane + 32 >= w1) b = bm[L * W + 32 + lane] & ~vis[32 + lane];
+    if (lane == w1) a &= first_mask;
+    if (lane + 32 == w1) b &= first_mask;
+    const unsigned ba = __ballot_sync(FULL, a != 0u), bb = __ballot_sync(FULL, b != 0u);
+    if (!(ba | bb)) return -1;
+    const int fl = ba ? __ffs(ba) - 1 : 32 + __ffs(bb) - 1;
+    const uint32_t word = __shfl_sync(FULL, fl < 32 ? a : b, fl & 31);
+    return fl * 32 + __ffs(word) - 1;
+  }
+  const int sfirst = w1 >> 5;
+  for (int sbase = sfirst & ~31; sbase < S; sbase += 32) {
+    const int sidx = sbase + lane;
+    uint32_t sw = (sidx < S && sidx >= sfirst) ? bms[L * S + sidx] : 0u;
+    if (sidx == sfirst) sw &= FULL << (w1 & 31);
+    unsigned bal = __ballot_sync(FULL, sw != 0u);
+    while (bal) {
+      const int fl = __ffs(bal) - 1;
+      const uint32_t swv = __shfl_sync(FULL, sw, fl);
+      const int widx = (sbase + fl) * 32 + lane;
+      uint32_t wv = ((swv >> lane) & 1u) ? bm[L * W + widx] & ~vis[widx] : 0u;
+      if (clear && ((swv >> lane) & 1u) && wv == 0u)
+        atomicAnd((uint32_t *)&bms[L * S + sbase + fl], ~(1u << lane));  // no unadded member
+      if (widx == w1) wv &= first_mask;
+      const unsigned bw = __ballot_sync(FULL, wv != 0u);
+      if (bw) {
+        const int ll = __ffs(bw) - 1;
+        const uint32_t word = __shfl_sync(FULL, wv, ll);
+        return ((sbase + fl) * 32 + ll) * 32 + __ffs(word) - 1;
+      }
+      bal &= bal - 1;
+    }
+  }
+  return -1;
+}
+
 // First contraction pass, on the item's own vertices (every super-vertex a
 // single vertex, every edge weight 1): the maximum-adjacency ordering with
-// keys capped at kcap, ties to the smallest id.  Each lane takes one
-// neighbour of the added vertex and moves it between buckets with
-// fire-and-forget atomics (a clear and a set touch different levels, and
-// bits of different neighbours never interfere); the entries whose key reaches kcap are marked (one bit per
-// adjacency entry) from a ballot, and the merges are applied afterwards by
-// the whole block.  Buckets of more than 64 words keep summary bits, set
-// eagerly and cleared lazily.  Returns whether anything merged; nrep
-// receives the merged sets labelled by their smallest id.
+// keys capped at kcap, ties to the smallest id, run by warp 0.
+//
+// A key grows by exactly one per step, so the key levels are cumulative
+// bitmaps (bit v of level L is set once v's key reaches L) and added
+// vertices are masked out by the vis bitmap (E; in registers, lane l holding
+// words l and l+32, when a level has at most 64 words).  With top = the
+// largest key of an unadded vertex, the added vertex X is always the
+// smallest unadded member of level top, so the next pick is one of: the
+// smallest neighbour whose key just rose above top (it alone has the new
+// largest key), the smaller of X's successor in level top and the smallest
+// neighbour that just reached top, or X's successor -- and only when level
+// top runs out is a level searched from scratch.  The successor search
+// does not depend on the key updates, so it overlaps them, and one packed
+// reduction gives the largest new key with its smallest holder.
+//
+// The step records only when each vertex was added (pos, F) and when each
+// key reached kcap (sat, H); the entry X -> j is contracted iff j was still
+// unadded when X was added and its key had reached kcap by then, which the
+// whole block evaluates afterwards into one bit per adjacency entry.  The
+// step is written without lane-divergent branches: lanes without work
+// write to per-lane dummy words or store the value every lane stores.  Returns whether anything merged; nrep receives
+// the merged sets labelled by their smallest id.
 template <typename IT>
 __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<IT> &m, int32_t *nrep,
                                               int n, int nsv, int kcap, int E, unsigned *err,
                                               Sh &sh) {
   const int W = m.W, S = m.S;
   const bool summaries = W > 64;
-  for (int i = threadIdx.x; i < n; i += RB) m.kst[i] = m.alive[i] ? 0 : 255;
-  for (int q = threadIdx.x; q < (E + 31) / 32 + 1; q += RB) m.ebits[q] = 0u;
-  buckets_init(m, (const int32_t *)nullptr, n, kcap);
+  uint32_t *vis_w = reinterpret_cast<uint32_t *>(m.E);
+  int32_t *pos = m.F, *sat = m.H;
+  uint32_t *sink = sh.sink;  // per-lane dummy targets
+  for (int i = threadIdx.x; i < n; i += RB) {
+    m.kst[i] = m.alive[i] ? 0 : 255;
+    sat[i] = 0x7fffffff;
+  }
+  for (int q = threadIdx.x; q < (kcap + 1) * W; q += RB) m.bm[q] = q < W ? FULL : 0u;
+  for (int q = threadIdx.x; q < (kcap + 1) * S; q += RB) {
+    const int nw = W - q * 32;  // level 0: every word has members
+    m.bms[q] = q < S ? (nw >= 32 ? FULL : (1u << nw) - 1u) : 0u;
+  }
+  for (int w = threadIdx.x; w < W; w += RB) {
+    uint32_t dead = 0u;  // dead vertices and the padding past n count as added
+    for (int b = 0; b < 32; ++b) {
+      const int v = w * 32 + b;
+      if (v >= n || !m.alive[v]) dead |= 1u << b;
+    }
+    vis_w[w] = dead;
+  }
+  __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    volatile uint32_t *bm = m.bm, *bms = m.bms, *eb = m.ebits;
+    volatile uint32_t *bm = m.bm, *bms = m.bms, *vis = vis_w;
     volatile uint8_t *kst = m.kst;
-    int contracted = 0;
     int top = 0;
-    long long rows = 0;
     const long long tp0 = P.prof ? clock64() : 0;
-    long long t_pick = 0, t_scan = 0;
-    const bool timing = P.prof != nullptr;
+    uint32_t va = 0u, vb = 0u;
+    if (!summaries) {
+      va = lane < W ? (uint32_t)vis[lane] : 0xffffffffu;
+      vb = lane + 32 < W ? (uint32_t)vis[32 + lane] : 0xffffffffu;
+    }
+    int X = next_member(bm, bms, vis, W, S, 0, -1, true);
     for (int step = 0; step < nsv; ++step) {
-      const long long c0 = timing ? clock64() : 0;
-      // pick: lowest set bit of the highest non-empty bucket
-      int X = -1;
-      for (;;) {
-        int cand = -1;
-        if (!summaries) {
-          const uint32_t w0 = lane < W ? bm[top * W + lane] : 0u;
-          const uint32_t w1 = lane + 32 < W ? bm[top * W + 32 + lane] : 0u;
-          const unsigned b0 = __ballot_sync(FULL, w0 != 0u);
-          const unsigned b1 = __ballot_sync(FULL, w1 != 0u);
-          if (b0 | b1) {
-            const int fl = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
-            const uint32_t word = __shfl_sync(FULL, fl < 32 ? w0 : w1, fl & 31);
-            cand = fl * 32 + __ffs(word) - 1;
-          }
-        } else {
-          for (int s0 = 0; s0 < S && cand < 0; s0 += 32) {
-            const uint32_t sw = s0 + lane < S ? bms[top * S + s0 + lane] : 0u;
-            unsigned b = __ballot_sync(FULL, sw != 0u);
-            while (b) {
-              const int fl = __ffs(b) - 1;
-              const uint32_t swv = __shfl_sync(FULL, sw, fl);
-              const int widx = (s0 + fl) * 32 + lane;
-              const uint32_t wv = ((swv >> lane) & 1u) ? bm[top * W + widx] : 0u;
-              const unsigned bb = __ballot_sync(FULL, wv != 0u);
-              if (bb) {
-                const int ll = __ffs(bb) - 1;
-                const uint32_t word = __shfl_sync(FULL, wv, ll);
-                cand = ((s0 + fl) * 32 + ll) * 32 + __ffs(word) - 1;
-                break;
-              }
-              if (lane == 0) bms[top * S + s0 + fl] = 0u;  // every word it covers is empty
-              b &= b - 1;
-            }
-          }
-        }
-        if (cand >= 0) {
-          X = cand;
-          break;
-        }
-        if (top == 0) break;
-        --top;
-      }
       if (X < 0) {
         if (lane == 0) atomicOr(err, DERR_INTERNAL);
         break;
       }
-      if (lane == 0) {
-        atomicAnd(&m.bm[top * W + (X >> 5)], ~(1u << (X & 31)));
-        kst[X] = 255;
+      pos[X] = step;
+      kst[X] = 255;
+      if (!summaries) {
+        const int xw = X >> 5;
+        const uint32_t xb = 1u << (X & 31);
+        va |= xw == lane ? xb : 0u;
+        vb |= xw == lane + 32 ? xb : 0u;
+      } else {
+        atomicOr(lane == 0 ? &vis_w[X >> 5] : &sink[lane], lane == 0 ? 1u << (X & 31) : 0u);
       }
       if (step == nsv - 1) break;
-      const long long c1 = timing ? clock64() : 0;
-      t_pick += c1 - c0;
+      int succ;
       const int b = m.off[X], e = m.off[X + 1];
-      rows += e - b;
-      int mx = 0;
+      int j0, ok0;
+      if (!summaries) {
+        // issue the successor's loads and the first neighbour loads before
+        // any of them is used, so that their latencies overlap
+        const int wt = top * W;
+        const uint32_t sa = lane < W ? bm[wt + lane] : 0u;
+        const uint32_t sb = lane + 32 < W ? bm[wt + 32 + lane] : 0u;
+        j0 = b + lane < e ? (int)m.adj[b + lane] : X;
+        const int p1 = X + 1, w1 = p1 >> 5;
+        const uint32_t fm = 0xffffffffu << (p1 & 31);
+        uint32_t a = lane >= w1 ? sa & ~va : 0u;
+        uint32_t c = lane + 32 >= w1 ? sb & ~vb : 0u;
+        a &= lane == w1 ? fm : 0xffffffffu;
+        c &= lane + 32 == w1 ? fm : 0xffffffffu;
+        ok0 = kst[j0];
+        const unsigned ba = __ballot_sync(FULL, a != 0u), bc = __ballot_sync(FULL, c != 0u);
+        const int fl = ba ? __ffs(ba) - 1 : 32 + __ffs(bc) - 1;
+        const uint32_t word = __shfl_sync(FULL, fl < 32 ? a : c, fl & 31);
+        succ = (ba | bc) ? fl * 32 + __ffs(word) - 1 : -1;
+      } else {
+        succ = next_member(bm, bms, vis, W, S, top, X, false);
+        j0 = b + lane < e ? (int)m.adj[b + lane] : X;
+        ok0 = kst[j0];
+      }
+      unsigned best = 0u;  // (new key << 24) | (0xffffff - id) of the moved neighbours
       for (int q0 = b; q0 < e; q0 += 32) {
         const int q = q0 + lane;
-        bool sat = false;
-        if (q < e) {
-          const int j = m.adj[q];
-          const int ok = kst[j];
-          if (ok != 255) {
-            const int nk = ok + 1 < kcap ? ok + 1 : kcap;
-            sat = nk >= kcap;
-            if (nk != ok) {
-              atomicAnd(&m.bm[ok * W + (j >> 5)], ~(1u << (j & 31)));
-              atomicOr(&m.bm[nk * W + (j >> 5)], 1u << (j & 31));
-              if (summaries) atomicOr(&m.bms[nk * S + (j >> 10)], 1u << ((j >> 5) & 31));
-              kst[j] = (uint8_t)nk;
-              mx = nk > mx ? nk : mx;
-            }
-          }
-        }
-        const unsigned sm = __ballot_sync(FULL, sat);
-        if (sm && lane == 0) {
-          // entries q0 + l for the set lanes l: two words at most
-          const int w = q0 >> 5, sh5 = q0 & 31;
-          eb[w] |= sm << sh5;
-          if (sh5) eb[w + 1] |= sm >> (32 - sh5);
-        }
-        contracted |= sm != 0u;
+        const int j = q0 == b ? j0 : (q < e ? (int)m.adj[q] : X);
+        const int ok = q0 == b ? ok0 : (int)kst[j];
+        const int nk = ok + 1 < kcap ? ok + 1 : kcap;
+        const bool moved = ok != 255 && nk != ok;
+        kst[moved ? j : X] = moved ? (uint8_t)nk : (uint8_t)255;
+        atomicOr(moved ? &m.bm[nk * W + (j >> 5)] : &sink[lane], moved ? 1u << (j & 31) : 0u);
+        if (summaries)
+          atomicOr(moved ? &m.bms[nk * S + (j >> 10)] : &sink[lane],
+                   moved ? 1u << ((j >> 5) & 31) : 0u);
+        sat[moved && nk >= kcap ? j : n] = step;  // H[n] is spare
+        const unsigned pk = ((unsigned)nk << 24) | (0xffffffu - (unsigned)j);
+        best = moved && pk > best ? pk : best;
       }
-      const long long c2 = timing ? clock64() : 0;
-      t_scan += c2 - c1;
-      mx = __reduce_max_sync(FULL, mx);
-      top = mx > top ? mx : top;
+      best = __reduce_max_sync(FULL, best);
+      const int mx = (int)(best >> 24);
+      const int arr = (int)(0xffffffu - (best & 0xffffffu));
+      if (best && mx > top) {
+        top = mx;
+        X = arr;
+      } else if (best && mx == top) {
+        X = succ < 0 ? arr : (succ < arr ? succ : arr);
+      } else if (succ >= 0) {
+        X = succ;
+      } else {
+        // level top has no unadded member left: the highest level that has
+        if (!summaries) {
+          if (lane < W) vis[lane] = va;
+          if (lane + 32 < W) vis[32 + lane] = vb;
+        }
+        __syncwarp();
+        X = -1;
+        while (top > 0 && X < 0) {
+          --top;
+          X = next_member(bm, bms, vis, W, S, top, -1, true);
+        }
+      }
       __syncwarp();
     }
     if (lane == 0) {
-      sh.contracted = contracted;
       sh.dbg[0] = P.prof ? clock64() - tp0 : 0;
-      sh.dbg[1] = t_pick;
       sh.dbg[2] = nsv;
-      sh.dbg[3] = t_scan;
     }
   }
   __syncthreads();
-  const bool any = sh.contracted != 0;
-  if (any) components(m, n, sh, nrep, m.ebits);
-  return any;
+  const long long tm0 = P.prof ? clock64() : 0;
+  // merge the ends of every entry a -> j whose key reached kcap while j was
+  // still unadded (union-find, root = smallest id); rows longer than 32
+  // entries are listed for whole warps
+  int32_t *lr = m.C;
+  for (int i = threadIdx.x; i < n; i += RB) nrep[i] = i;
+  if (threadIdx.x == 0) sh.ntouched = 0;
+  __syncthreads();
+  int any = 0;
+  for (int a = threadIdx.x; a < n; a += RB) {
+    if (!m.alive[a]) continue;
+    const int b0 = m.off[a], e0 = m.off[a + 1];
+    if (e0 - b0 > 32) {
+      lr[atomicAdd(&sh.ntouched, 1)] = a;
+      continue;
+    }
+    const int pa = pos[a];
+    for (int q = b0; q < e0; ++q) {
+      const int j = m.adj[q];
+      if (sat[j] <= pa && pa < pos[j]) {  // sat[j] <= pa implies j is alive
+        uf_union(nrep, a, j);
+        any = 1;
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nlr = sh.ntouched;
+    for (int k = warp; k < nlr; k += RW) {
+      const int a = lr[k], pa = pos[a];
+      for (int q = m.off[a] + lane; q < m.off[a + 1]; q += 32) {
+        const int j = m.adj[q];
+        if (sat[j] <= pa && pa < pos[j]) {
+          uf_union(nrep, a, j);
+          any = 1;
+        }
+      }
+    }
+  }
+  if (!__syncthreads_or(any)) return false;
+  for (int i = threadIdx.x; i < n; i += RB)
+    if (m.alive[i]) nrep[i] = uf_find(nrep, i);
+  __syncthreads();
+  if (P.prof && threadIdx.x == 0) sh.dbg[1] = clock64() - tm0;
+  return true;
+}
+
+// The ordering of ma_ordering() with the whole block scanning each added
+// super-vertex: for a few large super-vertices (later contraction passes
+// and Stoer-Wagner phases after the first pass contracted most edges), where
+// one warp walking thousands of member rows would dominate.  Warp 0 picks
+// (linear argmax, ties to the smallest id); same contract as ma_ordering().
+constexpr int BLOCK_NSV = 64;  // at most this many super-vertices
+
+template <typename IT>
+__device__ __forceinline__ void ma_ordering_block(const Mem<IT> &m, const int32_t *grp, int32_t *nrep,
+                                                  int nsv, int kcap, Sh &sh) {
+  int32_t *acc = m.E, *key = m.F, *touched = m.H, *svl = m.G;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int contracted = 0;
+  int s = -1, t = -1, cut = 0;
+  if (threadIdx.x == 0) sh.ntouched = 0;
+  for (int step = 0; step < nsv; ++step) {
+    if (warp == 0) {
+      unsigned long long best = 0;
+      for (int j = lane; j < nsv; j += 32) {
+        const int Y = svl[j];
+        if (!m.flag[Y]) {
+          const unsigned long long v = pack_key(key[Y], Y);
+          best = v > best ? v : best;
+        }
+      }
+      best = warp_max(best);
+      if (lane == 0) {
+        const int X = (int)(~(unsigned)(best & 0xffffffffu));
+        m.flag[X] = 1;
+        sh.sw_x = X;
+        sh.sw_key = (int)(best >> 32);
+      }
+    }
+    __syncthreads();
+    const int X = sh.sw_x;
+    s = t;
+    t = X;
+    cut = sh.sw_key;
+    if (step == nsv - 1) break;  // the last super-vertex has no unadded neighbour
+    const int mb = m.C[X], me = m.C[X + 1];
+    auto visit = [&](int e) {
+      const int j = m.adj[e];
+      if (!m.alive[j]) return;
+      const int Y = grp[j];
+      if (Y == X || m.flag[Y]) return;
+      if (atomicAdd(&acc[Y], 1) == 0) touched[atomicAdd(&sh.ntouched, 1)] = Y;
+    };
+    if (me - mb <= RW) {
+      // few members: a warp per member, lanes along its row
+      for (int q = mb + warp; q < me; q += RW) {
+        const int i = m.D[q];
+        for (int e = m.off[i] + lane; e < m.off[i + 1]; e += 32) visit(e);
+      }
+    } else {
+      for (int q = mb + threadIdx.x; q < me; q += RB) {
+        const int i = m.D[q];
+        for (int e = m.off[i]; e < m.off[i + 1]; ++e) visit(e);
+      }
+    }
+    __syncthreads();
+    const int nt = sh.ntouched;
+    for (int q = threadIdx.x; q < nt; q += RB) {
+      const int Y = touched[q];
+      const int a = acc[Y];
+      acc[Y] = 0;
+      int nk = key[Y] + a;
+      if (kcap > 0 && nk >= kcap) {
+        nk = kcap;
+        uf_union(nrep, X, Y);
+        contracted = 1;
+      }
+      key[Y] = nk;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh.ntouched = 0;  // ordered before the next scan by the pick's barrier
+  }
+  contracted = __syncthreads_or(contracted);
+  if (threadIdx.x == 0) {
+    sh.contracted = contracted;
+    sh.sw_s = s;
+    sh.sw_t = t;
+    sh.sw_cut = cut;
+  }
+  __syncthreads();
 }
 
 // A later contraction pass (super-vertices with several members, integer
@@ -871,6 +1102,179 @@ __device__ __forceinline__ void ma_pass_bucketed(const Mem<IT> &m, const int32_t
     if (lane == 0) sh.contracted = contracted;
   }
   __syncthreads();
+}
+
+// Exact acceptance test for lambda >= kcap by forest certificates.  Take
+// kcap-1 edge-disjoint spanning forests, each maximal in the edges the earlier
+// ones left.  An edge (u, v) in none of them has u and v joined by a path in
+// every forest (else that forest could have taken it) and by itself: kcap
+// edge-disjoint paths, so lambda(u, v) >= kcap and contracting u, v keeps
+// every cut below kcap (the sparse-certificate argument of Nagamochi and
+// Ibaraki).  Rounds repeat on the contracted multigraph (a super-vertex is
+// labelled by its smallest member; parallel edges stay separate copies).  One
+// super-vertex left certifies lambda >= kcap; that is exactly the item's
+// acceptance, whichever contraction reached it, so the result is the one the
+// canonical passes give.  A super-vertex of degree below kcap (lambda <
+// kcap), a round that contracts nothing, or the round limit gives up and the
+// canonical passes decide.
+//
+// Each forest is grown breadth-first, level-synchronously, from the smallest
+// vertex: every super-vertex of the frontier claims its unclaimed
+// neighbours over unused edges (compare-and-swap on the level).  An
+// unclaimed super-vertex that still has an unused edge starts a further
+// tree.  A tree edge is marked used on both of its adjacency entries (rows
+// are ascending, so the reverse entry is a binary search away).
+// Returns the rounds taken (> 0: certified) or minus the rounds tried.
+// Uses C, D, E, G, H, ebits.
+constexpr int FOREST_MAX_K = 16;       // at most 15 forests a round
+constexpr int FOREST_ROUNDS = 6;
+constexpr int FOREST_EXTRA_TREES = 16; // trees beyond the first per forest
+constexpr int FOREST_LONG_ROW = 32;    // rows longer than this go to a whole warp
+
+template <typename IT>
+__device__ __forceinline__ int find_entry(const Mem<IT> &m, int b, int a) {
+  int lo = m.off[b], hi = m.off[b + 1];
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((int)m.adj[mid] < a) lo = mid + 1; else hi = mid;
+  }
+  return lo;  // rows are symmetric, so a is there
+}
+
+// Calls f(a, q, b) for every adjacency entry q = (a -> b) of every alive
+// vertex a with sel(a): rows up to FOREST_LONG_ROW entries by one thread,
+// longer rows (listed in lr[0..nlr)) by a whole warp.
+template <typename IT, typename Sel, typename F>
+__device__ __forceinline__ void rows_pass(const Mem<IT> &m, int n, const int32_t *lr, int nlr,
+                                          Sel sel, F f) {
+  for (int a = threadIdx.x; a < n; a += RB) {
+    if (!m.alive[a]) continue;
+    const int b0 = m.off[a], e0 = m.off[a + 1];
+    if (e0 - b0 > FOREST_LONG_ROW || !sel(a)) continue;
+    for (int q = b0; q < e0; ++q) f(a, q, (int)m.adj[q]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < nlr; k += RW) {
+    const int a = lr[k];
+    if (!sel(a)) continue;
+    for (int q = m.off[a] + lane; q < m.off[a + 1]; q += 32) f(a, q, (int)m.adj[q]);
+  }
+}
+
+template <typename IT>
+__device__ __forceinline__ int forest_accept(const Mem<IT> &m, int n, int kcap, Sh &sh, bool prof) {
+  long long tc = prof ? clock64() : 0;
+  auto lap = [&](int k) {  // profile: cycles since the last lap into fdbg[k]
+    if (prof) {
+      const long long t = clock64();
+      if (threadIdx.x == 0) sh.fdbg[k] += t - tc;
+      tc = t;
+    }
+  };
+  int32_t *cf = m.C, *lvl = m.D, *lr = m.E, *rep = m.G, *deg = m.H;
+  uint32_t *used = m.ebits;
+  volatile int32_t *vl = lvl;
+  volatile uint32_t *vu = used;
+  const int E = m.off[n];
+  if (threadIdx.x == 0) {
+    sh.i0 = n;
+    sh.ntouched = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RB) {
+    cf[i] = i;
+    rep[i] = m.alive[i] ? i : -1;
+    if (m.alive[i]) {
+      atomicMin(&sh.i0, i);
+      if (m.off[i + 1] - m.off[i] > FOREST_LONG_ROW) lr[atomicAdd(&sh.ntouched, 1)] = i;
+    }
+  }
+  __syncthreads();
+  const int root = sh.i0, nlr = sh.ntouched;
+  auto all = [](int) { return true; };
+  auto is_used = [&](int q) { return (vu[q >> 5] >> (q & 31)) & 1u; };
+  for (int round = 1; round <= FOREST_ROUNDS; ++round) {
+    if (round > 1) {
+      for (int i = threadIdx.x; i < n; i += RB) deg[i] = 0;
+      __syncthreads();
+      rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
+        const int A = rep[a], B = rep[b];
+        if (B >= 0 && B != A) atomicAdd(&deg[A], 1);
+      });
+      __syncthreads();
+      int low = 0;
+      for (int i = threadIdx.x; i < n; i += RB) low |= rep[i] == i && deg[i] < kcap;
+      if (__syncthreads_or(low)) return -round;
+      lap(4);
+    }
+    for (int q = threadIdx.x; q < (E + 31) / 32; q += RB) used[q] = 0u;
+    for (int f = 1; f < kcap; ++f) {
+      for (int i = threadIdx.x; i < n; i += RB) lvl[i] = i == root ? 0 : -1;
+      int cur = 0;
+      for (int tree = 0;; ++tree) {
+        for (;;) {
+          __syncthreads();
+          int claimed = 0;
+          rows_pass(m, n, lr, nlr, [&](int a) { return vl[rep[a]] == cur; },
+                    [&](int a, int q, int b) {
+                      const int B = rep[b];
+                      if (B < 0 || B == rep[a] || vl[B] != -1 || is_used(q)) return;
+                      if (atomicCAS(&lvl[B], -1, cur + 1) == -1) {
+                        atomicOr(&used[q >> 5], 1u << (q & 31));
+                        const int r = find_entry(m, b, a);
+                        atomicOr(&used[r >> 5], 1u << (r & 31));
+                        claimed = 1;
+                      }
+                    });
+          if (prof && threadIdx.x == 0) sh.fdbg[1] += 1;
+          if (!__syncthreads_or(claimed)) break;
+          ++cur;
+        }
+        lap(0);
+        // the forest is maximal unless an unclaimed super-vertex still has an
+        // unused edge (its other end is unclaimed too: a claimed end would
+        // have claimed it)
+        if (threadIdx.x == 0) sh.i0 = 0x7fffffff;
+        __syncthreads();
+        rows_pass(m, n, lr, nlr, [&](int a) { return vl[rep[a]] == -1; },
+                  [&](int a, int q, int b) {
+                    const int A = rep[a], B = rep[b];
+                    if (B >= 0 && B != A && !is_used(q)) atomicMin(&sh.i0, A);
+                  });
+        __syncthreads();
+        lap(2);
+        const int X = sh.i0;
+        if (X == 0x7fffffff) break;
+        if (prof && threadIdx.x == 0) sh.fdbg[3] += 1;
+        if (tree >= FOREST_EXTRA_TREES) return -round;
+        ++cur;
+        if (threadIdx.x == 0) lvl[X] = cur;
+      }
+    }
+    __syncthreads();
+    int merged = 0;
+    rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
+      if (b < a) return;  // each undirected edge once
+      const int A = rep[a], B = rep[b];
+      if (B < 0 || B == A || is_used(q)) return;
+      merged |= uf_link(cf, A, B);
+    });
+    if (!__syncthreads_or(merged)) return -round;
+    lap(4);
+    int roots = 0;
+    for (int i = threadIdx.x; i < n; i += RB) {
+      const int r = rep[i];
+      if (r >= 0) {
+        const int nr = uf_find(cf, r);
+        rep[i] = nr;
+        roots += nr == i;
+      }
+    }
+    const int nroots = block_sum_int(roots, sh);
+    lap(5);
+    if (nroots == 1) return round;
+  }
+  return -FOREST_ROUNDS;
 }
 
 template <typename IT>
@@ -1053,7 +1457,17 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
   int32_t *rep = m.A, *nrep = m.B;
   int nsv = 1, passes = 0;
-  {
+  bool certified = false;
+  if (kcap <= FOREST_MAX_K && P.forest_min_n > 0 && nalive >= P.forest_min_n) {
+    const long long f0 = P.prof ? clock64() : 0;
+    const int fr = forest_accept(m, n, kcap, sh, P.prof != nullptr);
+    certified = fr > 0;
+    if (P.prof && threadIdx.x == 0) {
+      sh.pf_forest = fr;
+      sh.pf_forest_cycles = clock64() - f0;
+    }
+  }
+  if (!certified) {
     nsv = nalive;
     bool more = true;
     const bool bucketed = kcap < KB_LEVELS && n < (1 << 24);  // pick packs the id in 24 bits
@@ -1061,30 +1475,44 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
       if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
       ++passes;
       const bool any = ma_pass_first(P, m, nrep, n, nalive, kcap, E, &P.ctr->error, sh);
-      for (int i = threadIdx.x; i < n; i += RB) rep[i] = m.alive[i] ? (any ? nrep[i] : i) : -1;
-      __syncthreads();
+      int r1 = 0;
+      for (int i = threadIdx.x; i < n; i += RB) {
+        const int r = m.alive[i] ? (any ? nrep[i] : i) : -1;
+        rep[i] = r;
+        r1 += r == i;
+      }
+      nsv = block_sum_int(r1, sh);
       more = any;
+      if (P.prof && threadIdx.x == 0) sh.pf_nsv1 = nsv;
     } else {
       for (int i = threadIdx.x; i < n; i += RB) rep[i] = m.alive[i] ? i : -1;
       __syncthreads();
     }
-    while (more) {
+    const long long tl0 = P.prof ? clock64() : 0;
+    while (more && nsv > 1) {
       nsv = group_members(m, rep, n, sh);
-      if (nsv <= 1) break;
       reset_ma_state(m, n);
       for (int i = threadIdx.x; i < n; i += RB) nrep[i] = i;
       __syncthreads();
       if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
       ++passes;
-      if (bucketed)
+      if (nsv <= BLOCK_NSV)
+        ma_ordering_block(m, rep, nrep, nsv, kcap, sh);
+      else if (bucketed)
         ma_pass_bucketed(m, rep, nrep, n, nsv, kcap, &P.ctr->error, sh);
       else
         ma_ordering(m, rep, nrep, nsv, kcap, sh);
       if (!sh.contracted) break;
-      for (int i = threadIdx.x; i < n; i += RB)
-        if (m.alive[i]) rep[i] = uf_find(nrep, rep[i]);
-      __syncthreads();
+      int roots = 0;
+      for (int i = threadIdx.x; i < n; i += RB) {
+        if (!m.alive[i]) continue;
+        const int r = uf_find(nrep, rep[i]);
+        rep[i] = r;
+        roots += r == i;
+      }
+      nsv = block_sum_int(roots, sh);
     }
+    if (P.prof && threadIdx.x == 0) sh.dbg[3] = clock64() - tl0;
   }
   if (threadIdx.x == 0) {
     sh.pf_passes = passes;
@@ -1114,7 +1542,10 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
       group_members(m, grp, n, sh);
       reset_ma_state(m, n);
       if (threadIdx.x == 0) add_ll(&ctr->sw_phases, 1ll);
-      ma_ordering(m, grp, (int32_t *)nullptr, nsv, 0, sh);
+      if (nsv <= BLOCK_NSV)
+        ma_ordering_block(m, grp, (int32_t *)nullptr, nsv, 0, sh);
+      else
+        ma_ordering(m, grp, (int32_t *)nullptr, nsv, 0, sh);
       const int s = sh.sw_s, t = sh.sw_t, cut = sh.sw_cut;
       if (cut < best) {
         best = cut;
@@ -1177,7 +1608,7 @@ __device__ int run_item(const RefineParams &P, unsigned long long seq, const Ite
 // ends when nothing is pending and the queue is closed, or (open, serving)
 // when nothing has been pending for idle_limit_ns; a wait for work that is
 // pending but never published ends at wait_limit_ns with DERR_TIMEOUT.
-__global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
+__global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
   __shared__ Sh sh;
   char *slab = P.slab + (size_t)blockIdx.x * P.slab_bytes;
   RunCounters *ctr = P.ctr;
@@ -1250,6 +1681,10 @@ __global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
       for (int k = 0; k < 9; ++k) sh.ts[k] = t;
       sh.used_slab = 0;
       sh.pf_E = sh.pf_nalive = sh.pf_passes = sh.pf_nsv = -1;
+      sh.pf_forest = sh.pf_nsv1 = 0;
+      sh.pf_forest_cycles = 0;
+      sh.pf_t0 = (long long)globaltimer_ns();
+      for (int k = 0; k < 6; ++k) sh.fdbg[k] = 0;
       for (int k = 0; k < 4; ++k) sh.dbg[k] = 0;
     }
     __syncthreads();
@@ -1276,8 +1711,13 @@ __global__ void __launch_bounds__(RB) k_refine(RefineParams P) {
         q->slab = sh.used_slab;
         q->top = (int)(it.flags & ITEM_TOP);
         for (int k = 0; k < 8; ++k) q->dt[k] = (unsigned)(sh.ts[k + 1] - sh.ts[k]);
-        q->t_begin = sh.ts[0];
+        q->t_begin = sh.pf_t0;
+        q->t_end = (long long)globaltimer_ns();
         for (int k = 0; k < 4; ++k) q->dbg[k] = sh.dbg[k];
+        q->forest = sh.pf_forest;
+        q->nsv1 = sh.pf_nsv1;
+        q->forest_cycles = sh.pf_forest_cycles;
+        for (int k = 0; k < 6; ++k) q->fdbg[k] = sh.fdbg[k];
       }
     }
     if (threadIdx.x == 0) {
