@@ -134,6 +134,9 @@ struct Sh {
   long long pf_forest_cycles, pf_t0;
   long long fdbg[6];
   uint32_t sink[32];  // per-lane dummy targets of branch-free warp code
+  int32_t duf[32];    // dense finish: merges of one pass (union-find over indices)
+  uint32_t dside;     // dense finish: side of the minimum cut (mask of indices)
+  int32_t dcut, dpasses, dphases;
 };
 
 // Outcome of one item.
@@ -819,6 +822,79 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
       vb = lane + 32 < W ? (uint32_t)vis[32 + lane] : 0xffffffffu;
     }
     int X = next_member(bm, bms, vis, W, S, 0, -1, true);
+    if (!summaries) {
+      // levels of at most 64 words: lane l reads words l and l+32 (clamped
+      // to the last word; the masks drop the clamped copies)
+      const int la = lane < W ? lane : W - 1, lb = lane + 32 < W ? lane + 32 : W - 1;
+      for (int step = 0; step < nsv; ++step) {
+        if (X < 0) {
+          if (lane == 0) atomicOr(err, DERR_INTERNAL);
+          break;
+        }
+        pos[X] = step;
+        kst[X] = 255;
+        const int xw = X >> 5;
+        const uint32_t xb = 1u << (X & 31);
+        va |= xw == lane ? xb : 0u;
+        vb |= xw == lane + 32 ? xb : 0u;
+        if (step == nsv - 1) break;
+        const int b = m.off[X], e = m.off[X + 1];
+        const uint32_t sa = bm[top * W + la], sb = bm[top * W + lb];
+        const int q = b + lane;
+        const int jr = (int)m.adj[q < e ? q : b];
+        const int j = q < e ? jr : X;
+        // successor of X in level top, packed like a key update
+        const int p1 = X + 1, w1 = p1 >> 5;
+        const uint32_t fm = 0xffffffffu << (p1 & 31);
+        uint32_t wa = (lane < W && lane >= w1) ? sa & ~va : 0u;
+        uint32_t wb = (lane + 32 < W && lane + 32 >= w1) ? sb & ~vb : 0u;
+        wa &= lane == w1 ? fm : 0xffffffffu;
+        wb &= lane + 32 == w1 ? fm : 0xffffffffu;
+        const int ok = kst[j];
+        const unsigned ba = __ballot_sync(FULL, wa != 0u), bb = __ballot_sync(FULL, wb != 0u);
+        const int fl = ba ? __ffs(ba) - 1 : 32 + __ffs(bb) - 1;
+        const uint32_t word = __shfl_sync(FULL, fl < 32 ? wa : wb, fl & 31);
+        const int succ = fl * 32 + __ffs(word) - 1;
+        const unsigned ks = (ba | bb) ? ((unsigned)top << 24) | (0xffffffu - (unsigned)succ) : 0u;
+        // key update of the first 32 neighbours (ok < kcap: unadded, not capped)
+        const bool moved = ok < kcap;
+        const int nk = ok + 1;
+        kst[moved ? j : X] = moved ? (uint8_t)nk : (uint8_t)255;
+        atomicOr(moved ? &m.bm[nk * W + (j >> 5)] : &sink[lane], moved ? 1u << (j & 31) : 0u);
+        sat[moved && nk == kcap ? j : n] = step;  // H[n] is spare
+        unsigned pk = moved ? ((unsigned)nk << 24) | (0xffffffu - (unsigned)j) : 0u;
+        pk = pk > ks ? pk : ks;
+        for (int q0 = b + 32; q0 < e; q0 += 32) {  // rows longer than 32 entries
+          const int qq = q0 + lane;
+          const int jj = qq < e ? (int)m.adj[qq] : X;
+          const int o2 = kst[jj];
+          const bool mv2 = o2 < kcap;
+          const int n2 = o2 + 1;
+          kst[mv2 ? jj : X] = mv2 ? (uint8_t)n2 : (uint8_t)255;
+          atomicOr(mv2 ? &m.bm[n2 * W + (jj >> 5)] : &sink[lane], mv2 ? 1u << (jj & 31) : 0u);
+          sat[mv2 && n2 == kcap ? jj : n] = step;
+          const unsigned p2 = mv2 ? ((unsigned)n2 << 24) | (0xffffffu - (unsigned)jj) : 0u;
+          pk = p2 > pk ? p2 : pk;
+        }
+        // the largest key, then the smallest id: the next vertex to add
+        pk = __reduce_max_sync(FULL, pk);
+        if (pk != 0u && (int)(pk >> 24) >= top) {
+          top = (int)(pk >> 24);
+          X = (int)(0xffffffu - (pk & 0xffffffu));
+        } else {
+          // level top has no unadded member left: the highest level that has
+          if (lane < W) vis[lane] = va;
+          if (lane + 32 < W) vis[32 + lane] = vb;
+          __syncwarp();
+          X = -1;
+          while (top > 0 && X < 0) {
+            --top;
+            X = next_member(bm, bms, vis, W, S, top, -1, true);
+          }
+        }
+        __syncwarp();
+      }
+    } else {
     for (int step = 0; step < nsv; ++step) {
       if (X < 0) {
         if (lane == 0) atomicOr(err, DERR_INTERNAL);
@@ -901,6 +977,7 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
         }
       }
       __syncwarp();
+    }
     }
     if (lane == 0) {
       sh.dbg[0] = P.prof ? clock64() - tp0 : 0;
@@ -1277,6 +1354,137 @@ __device__ __forceinline__ int forest_accept(const Mem<IT> &m, int n, int kcap, 
   return -FOREST_ROUNDS;
 }
 
+// ---- few super-vertices: a dense finish ---------------------------------------
+// With at most 32 super-vertices left (indexed in ascending order of their
+// smallest member, so index order is id order), their integer edge weights
+// fit a small matrix w[nsv][nsv] and one warp runs the remaining capped
+// contraction passes and the Stoer-Wagner phases on it, lane l holding
+// super-vertex l, with exactly the rules of the sparse passes: largest key,
+// ties to the smallest id; in a capped pass every X-Y whose key reaches kcap
+// when X is added merges (survivor: the smaller id); a phase's cut is the key
+// of the last super-vertex t, the earliest minimum is kept, its side is t's
+// members, and t merges into the one added before it.
+constexpr int DENSE_NSV = 32;
+
+// Adds row and column l of w into r (r < l), zeroes r's diagonal.  Warp 0.
+__device__ __forceinline__ void dense_fold(int32_t *w, int nsv, int r, int l) {
+  const int c = threadIdx.x & 31;
+  if (c < nsv) w[r * nsv + c] += w[l * nsv + c];
+  __syncwarp();
+  if (c < nsv) w[c * nsv + r] += w[c * nsv + l];
+  __syncwarp();
+  if (c == 0) w[r * nsv + r] = 0;
+  __syncwarp();
+}
+
+// One maximum-adjacency ordering over the live indices (mask live); kcap > 0
+// caps keys and records merges in duf; kcap == 0 reports s, t and the cut.
+__device__ __forceinline__ void dense_order(const int32_t *w, int nsv, uint32_t live, int kcap,
+                                            int32_t *duf, int &s, int &t, int &cut, bool &merged) {
+  const int l = threadIdx.x & 31;
+  long long key = 0;
+  bool added = !((live >> l) & 1u);
+  const int cnt = __popc(live);
+  s = t = -1;
+  cut = 0;
+  merged = false;
+  for (int step = 0; step < cnt; ++step) {
+    // largest key, ties to the smallest index
+    const unsigned long long pk =
+        added ? 0ull : (((unsigned long long)key << 6) | (unsigned long long)(63 - l)) + 1ull;
+    unsigned long long best = pk;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(FULL, best, o);
+      best = x > best ? x : best;
+    }
+    const int X = 63 - (int)((best - 1ull) & 63ull);
+    s = t;
+    t = X;
+    cut = (int)((best - 1ull) >> 6);
+    added |= l == X;
+    const int wx = l < nsv ? w[X * nsv + l] : 0;
+    if (!added && wx > 0) {
+      long long nk = key + wx;
+      if (kcap > 0 && nk >= kcap) {
+        nk = kcap;
+        // merge l into X's set (duf links point to smaller indices)
+        volatile int32_t *vd = duf;
+        int a = X, b = l;
+        for (;;) {
+          while (vd[a] != a) a = vd[a];
+          while (vd[b] != b) b = vd[b];
+          if (a == b) break;
+          if (a > b) { const int tt = a; a = b; b = tt; }
+          if (atomicCAS(&duf[b], b, a) == b) break;
+        }
+        merged = true;
+      }
+      key = nk;
+    }
+    __syncwarp();
+  }
+  merged = __any_sync(FULL, merged);
+}
+
+// Runs the dense finish on w; fills sh.dside (side mask over the initial
+// indices, when the item fails), sh.dcut (the minimum cut, or -1 when the
+// contraction left one super-vertex: accept), sh.dpasses, sh.dphases.
+__device__ void dense_finish(int32_t *w, int nsv, int kcap, Sh &sh) {
+  if (threadIdx.x >= 32) return;
+  const int l = threadIdx.x;
+  uint32_t live = nsv >= 32 ? 0xffffffffu : (1u << nsv) - 1u;
+  uint32_t mem = 1u << l;  // lane l: the initial indices it holds
+  int passes = 0, phases = 0;
+  bool more = true;
+  while (more && __popc(live) > 1) {
+    sh.duf[l] = l;
+    __syncwarp();
+    int s, t, cut;
+    bool merged;
+    dense_order(w, nsv, live, kcap, sh.duf, s, t, cut, merged);
+    ++passes;
+    more = merged;
+    if (!merged) break;
+    // fold every merged index into its root, in ascending order
+    volatile int32_t *vd = sh.duf;
+    for (int x = 0; x < nsv; ++x) {
+      if (!((live >> x) & 1u)) continue;
+      int r = x;
+      while (vd[r] != r) r = vd[r];
+      if (r == x) continue;
+      dense_fold(w, nsv, r, x);
+      const uint32_t mx = __shfl_sync(FULL, mem, x);
+      if (l == r) mem |= mx;
+      live &= ~(1u << x);
+    }
+  }
+  int best = -1;
+  uint32_t side = 0u;
+  while (__popc(live) > 1) {
+    int s, t, cut;
+    bool merged;
+    dense_order(w, nsv, live, 0, sh.duf, s, t, cut, merged);
+    ++phases;
+    if (best < 0 || cut < best) {
+      best = cut;
+      side = __shfl_sync(FULL, mem, t);
+    }
+    const int lo = s < t ? s : t, hi = s < t ? t : s;
+    dense_fold(w, nsv, lo, hi);
+    const uint32_t mh = __shfl_sync(FULL, mem, hi);
+    if (l == lo) mem |= mh;
+    live &= ~(1u << hi);
+  }
+  if (l == 0) {
+    sh.dcut = best;
+    sh.dside = side;
+    sh.dpasses = passes;
+    sh.dphases = phases;
+  }
+  __syncwarp();
+}
+
 template <typename IT>
 __device__ __forceinline__ void reset_ma_state(const Mem<IT> &m, int n) {
   for (int i = threadIdx.x; i < n; i += RB) {
@@ -1457,6 +1665,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
   int32_t *rep = m.A, *nrep = m.B;
   int nsv = 1, passes = 0;
+  int dense_cut = -1;  // >= 0: the dense finish found the cut (side in m.side)
   bool certified = false;
   if (kcap <= FOREST_MAX_K && P.forest_min_n > 0 && nalive >= P.forest_min_n) {
     const long long f0 = P.prof ? clock64() : 0;
@@ -1489,6 +1698,66 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
       __syncthreads();
     }
     const long long tl0 = P.prof ? clock64() : 0;
+    if (bucketed && more && nsv > 1 && nsv <= DENSE_NSV && nsv * nsv <= 2 * (n + 1)) {
+      // few super-vertices left: their weight matrix, then the dense finish
+      int32_t *idx = m.C, *lr = m.D, *rank = m.H;
+      int32_t *w = reinterpret_cast<int32_t *>(m.wide);
+      for (int i = threadIdx.x; i < n; i += RB) rank[i] = (m.alive[i] && rep[i] == i) ? 1 : 0;
+      for (int q = threadIdx.x; q < nsv * nsv; q += RB) w[q] = 0;
+      if (threadIdx.x == 0) sh.ntouched = 0;
+      __syncthreads();
+      block_scan_array(rank, n, sh);
+      for (int i = threadIdx.x; i < n; i += RB)
+        if (m.alive[i] && rep[i] == i) idx[i] = rank[i];
+      __syncthreads();
+      // every entry between two super-vertices (each edge from both ends)
+      for (int a = threadIdx.x; a < n; a += RB) {
+        if (!m.alive[a]) continue;
+        const int b0 = m.off[a], e0 = m.off[a + 1];
+        if (e0 - b0 > 32) {
+          lr[atomicAdd(&sh.ntouched, 1)] = a;
+          continue;
+        }
+        const int A = idx[rep[a]];
+        for (int q = b0; q < e0; ++q) {
+          const int r = rep[m.adj[q]];
+          if (r < 0) continue;
+          const int B = idx[r];
+          if (B != A) atomicAdd(&w[A * nsv + B], 1);
+        }
+      }
+      __syncthreads();
+      {
+        const int nl = sh.ntouched;
+        for (int k = warp; k < nl; k += RW) {
+          const int a = lr[k], A = idx[rep[a]];
+          for (int q = m.off[a] + lane; q < m.off[a + 1]; q += 32) {
+            const int r = rep[m.adj[q]];
+            if (r < 0) continue;
+            const int B = idx[r];
+            if (B != A) atomicAdd(&w[A * nsv + B], 1);
+          }
+        }
+      }
+      __syncthreads();
+      dense_finish(w, nsv, kcap, sh);
+      __syncthreads();
+      passes += sh.dpasses;
+      if (threadIdx.x == 0) {
+        add_ll(&ctr->ni_passes, (long long)sh.dpasses);
+        add_ll(&ctr->sw_phases, (long long)sh.dphases);
+      }
+      if (sh.dcut < 0) {
+        nsv = 1;
+      } else {
+        dense_cut = sh.dcut;
+        const uint32_t side = sh.dside;
+        for (int i = threadIdx.x; i < n; i += RB)
+          m.side[i] = m.alive[i] && ((side >> idx[rep[i]]) & 1u);
+        __syncthreads();
+      }
+      more = false;
+    }
     while (more && nsv > 1) {
       nsv = group_members(m, rep, n, sh);
       reset_ma_state(m, n);
@@ -1535,7 +1804,12 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   }
 
   // 6. canonical Stoer-Wagner on the contracted graph; grp = A (starts as rep)
-  {
+  if (dense_cut >= 0) {
+    if (dense_cut > T) {
+      if (threadIdx.x == 0) atomicOr(&P.ctr->error, DERR_INTERNAL);
+      return OUT_ERROR;
+    }
+  } else {
     int32_t *grp = m.A;
     int best = 0x7fffffff;
     while (nsv > 1) {
