@@ -184,6 +184,24 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ traffic
+def profiled_traffic():
+    """DRAM bytes per k_refine launch from the committed ncu capture, or None
+    when the kernel sources have changed since the counters were taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_refine_lfr_100k.traffic.json")
+    try:
+        rec = json.load(open(prof))
+        h = hashlib.sha256()
+        for src in rec["kernel_sources"]:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        if h.hexdigest() != rec["kernel_sources_sha256"]:
+            return None
+        return rec["traffic_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 # ------------------------------------------------------------------ ranks
 def aggregate_ranks(dist, torch, dev, total_ms: float, m: int, clusters: int):
     """Weak scaling across ranks: every rank refines its own instance with no
@@ -393,12 +411,7 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": peak_kind, "alg_bytes_per_launch": r_bytes,
                 "ms_per_launch": r_ms, "share_of_step": r_ms / (total_ms / args.steps)}
-    prof = os.path.join(ROOT, "profiles", "k_refine_lfr_100k.traffic.json")
-    if os.path.exists(prof):
-        try:
-            roofline["traffic"] = json.load(open(prof)).get("traffic_bytes_per_launch")
-        except (OSError, ValueError):
-            pass
+    roofline["traffic"] = profiled_traffic()
 
     serving = None
     if args.serving_requests > 0:

@@ -136,6 +136,15 @@ int forest_min_n_config() {
   return (int)v;
 }
 
+// Most super-vertices left after the first contraction pass that the dense
+// finish takes (WCC_DENSE_NSV, at most 32; 0 keeps every item on the sparse
+// passes).
+int dense_max_config() {
+  const char *e = getenv("WCC_DENSE_NSV");
+  long long v = e ? atoll(e) : 32;
+  return (int)(v < 0 ? 0 : v > 32 ? 32 : v);
+}
+
 // Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
 // largest a CTA can opt into, one CTA per SM).  Items whose working set is
 // larger use a global slab.
@@ -383,6 +392,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     p.smem_bytes = smem_bytes;
     p.slab_bytes = slab_bytes;
     p.forest_min_n = forest_min_n_config();
+    p.dense_max = dense_max_config();
     // optional per-item profile (WCC_PROFILE_ITEMS=<csv path>)
     const char *prof_path = getenv("WCC_PROFILE_ITEMS");
     DevBuf prof_buf;

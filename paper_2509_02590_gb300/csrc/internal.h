@@ -144,6 +144,7 @@ struct RefineParams {
   size_t slab_bytes;          // per CTA
   size_t smem_bytes;          // dynamic shared memory per CTA
   int forest_min_n;           // smallest item that tries the forest acceptance test (0 = never)
+  int dense_max;              // most super-vertices the dense finish takes (0 = never)
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
   ItemProf *prof;             // optional per-item profile (NULL = off)
@@ -200,6 +201,7 @@ int current_device();                       // fails with WCC_ERR_CUDA without a
 uint64_t wait_limit_ns();                   // WCC_WAIT_LIMIT_MS (default 30 s)
 size_t refine_smem_bytes_config(int device);  // WCC_SMEM_KB (default: opt-in maximum)
 int forest_min_n_config();                    // WCC_FOREST_MIN_N
+int dense_max_config();                       // WCC_DENSE_NSV
 wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule);
 
 template <typename T>

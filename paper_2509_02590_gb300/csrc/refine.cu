@@ -1364,7 +1364,8 @@ __device__ __forceinline__ int forest_accept(const Mem<IT> &m, int n, int kcap, 
 // when X is added merges (survivor: the smaller id); a phase's cut is the key
 // of the last super-vertex t, the earliest minimum is kept, its side is t's
 // members, and t merges into the one added before it.
-constexpr int DENSE_NSV = 32;
+constexpr int DENSE_NSV = 32;  // one lane per super-vertex
+static_assert(DENSE_NSV <= 32, "the dense finish keeps one super-vertex per lane");
 
 // Adds row and column l of w into r (r < l), zeroes r's diagonal.  Warp 0.
 __device__ __forceinline__ void dense_fold(int32_t *w, int nsv, int r, int l) {
@@ -1698,7 +1699,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
       __syncthreads();
     }
     const long long tl0 = P.prof ? clock64() : 0;
-    if (bucketed && more && nsv > 1 && nsv <= DENSE_NSV && nsv * nsv <= 2 * (n + 1)) {
+    if (bucketed && more && nsv > 1 && nsv <= P.dense_max && nsv * nsv <= 2 * (n + 1)) {
       // few super-vertices left: their weight matrix, then the dense finish
       int32_t *idx = m.C, *lr = m.D, *rank = m.H;
       int32_t *w = reinterpret_cast<int32_t *>(m.wide);

@@ -222,6 +222,7 @@ void launch_kernel(Server *S) {
   p.idle_limit_ns = IDLE_LIMIT_NS;
   p.smem_bytes = S->smem_bytes;
   p.forest_min_n = forest_min_n_config();
+  p.dense_max = dense_max_config();
   p.slab = S->slab.as<char>();
   p.slab_bytes = S->slab_bytes;
   launch_refine(p, S->grid, true, S->kstream);

@@ -178,3 +178,39 @@ def test_min_labels_consistent(wcc):
     ref, _, _, _ = _oracle(w)
     out, _ = _gpu(wcc, w)
     assert np.array_equal(min_labels(out), min_labels(ref))
+
+
+def _random_workload(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(500, 4000))
+    k = int(rng.integers(2, 12))
+    lab = rng.integers(0, k, n).astype(np.int32)
+    src, dst = [], []
+    for c in range(k):
+        vs = np.nonzero(lab == c)[0]
+        if len(vs) < 2:
+            continue
+        a, b = synth.random_gnp(len(vs), float(rng.uniform(0.01, 0.2)), rng)
+        src.append(vs[a]); dst.append(vs[b])
+    a, b = synth.random_gnp(n, 2.0 / n, rng)
+    src.append(a); dst.append(b)
+    s, d = synth.graphs._dedup(n, np.concatenate(src), np.concatenate(dst))
+    return synth.Workload("rand", n, s, d, lab, 2)
+
+
+# Internal strategy switches (each must leave the result unchanged): the
+# sparse passes only, the forest acceptance test on every item, and working
+# memory in the global slab instead of shared memory.
+@pytest.mark.parametrize("env", [{"WCC_DENSE_NSV": "0"}, {"WCC_FOREST_MIN_N": "2"},
+                                 {"WCC_SMEM_KB": "40"},
+                                 {"WCC_DENSE_NSV": "0", "WCC_FOREST_MIN_N": "2", "WCC_SMEM_KB": "40"}])
+def test_strategy_switches_keep_results(wcc, monkeypatch, env):
+    cases = [synth.planted_1k(0), synth.lfr_like(12000, seed=8)] + [_random_workload(s) for s in range(3)]
+    refs = [_oracle(w)[0] for w in cases]
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    for w, ref in zip(cases, refs):
+        out, _ = _gpu(wcc, w)
+        assert np.array_equal(out, ref), (w.name, env)
+        out, _ = _gpu(wcc, w, mode="plain", device=False)
+        assert np.array_equal(out, ref), (w.name, env, "plain")
