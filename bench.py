@@ -6,12 +6,24 @@ edge list (wcc_create_graph_from_edges) + the refinement (wcc_run: grouping by
 input label, refinement kernel, output numbering).  Inputs (edge list and input
 clustering) are resident in HBM when the timed region starts; L2 is flushed
 (a 512 MiB device write) before every timed step, outside the step's events.
+The line also reports the refinement alone on a resident graph
+("graph_resident") and the CSR build time.
 
-Workload: the LFR-style benchmark graph with 100,000 vertices (power-law
-degrees, exponent 2.5, mean 20, max 1,000; power-law community sizes 20-2,000,
-exponent 1.5; mixing 0.3; 10% of communities merged pairwise through 1-2
-bridges), seed = rank, criterion floor(log10 n), min size 2 (s_pre = s_post =
-1 as in the paper's experiments).
+Workloads (--workload; the default is the one the driver times):
+  lfr_100k   LFR-style graph, 100,000 vertices (power-law degrees, exponent
+             2.5, mean 20, max 1,000; power-law community sizes 20-2,000,
+             exponent 1.5; mixing 0.3; 10% of communities merged pairwise
+             through 1-2 bridges), seed = rank, criterion floor(log10 n), min
+             size 2 (s_pre = s_post = 1 as in the paper's experiments);
+  planted_1k 1,010-vertex planted partition (20 blocks of 50, 4 bridged, 10
+             pendant vertices), min size 11; the plain path is its headline;
+  dcpp_10m   degree-corrected planted partition, 10M vertices, ~200M edges,
+             power-law cluster sizes 10-50,000, 5% chain clusters;
+  dcpp_100m  100M vertices, ~2B edges, 5M clusters on [10, 100,000], 3%
+             bridged two-part clusters (about 100 GB of device memory).
+The two large ones are generated on the GPU; their plain path (one launch per
+work item, millions of items) is not run, and their CPU baseline is the oracle
+on a seeded sample of input clusters (each refines independently).
 
 Multi-GPU (torchrun): input clusters are independent (Algorithms 1-2 iterate
 over them with no exchange), so each rank refines its own instance with no
@@ -35,20 +47,39 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "WCC clusters/s and edges/s at 1 GB300 (batched/served vs plain), %HBM roofline; p50/p99"
-WORKLOAD = "lfr_100k"
-MIN_SIZE = 2
+WORKLOADS = ("lfr_100k", "planted_1k", "dcpp_10m", "dcpp_100m")
+LARGE = ("dcpp_10m", "dcpp_100m")
 
 
-def workload(rank: int):
+def workload(name: str, rank: int):
     import synth
-    return synth.lfr_like(100_000, seed=rank, min_size=MIN_SIZE)
+    if name == "lfr_100k":
+        return synth.lfr_like(100_000, seed=rank, min_size=2)
+    if name == "planted_1k":
+        return synth.planted_1k(seed=rank)
+    from synth import gpu_graphs
+    if name == "dcpp_10m":
+        return gpu_graphs.dcpp_10m(seed=rank)
+    return gpu_graphs.dcpp_100m(seed=rank)
 
 
-def describe(w) -> dict:
-    return {"workload": f"{WORKLOAD}: LFR-style graph, {w.n} vertices, {w.m} undirected edges, "
-                        f"{w.n_clusters} input clusters (10% merged pairwise by 1-2 bridges), "
-                        "criterion floor(log10 n), min size 2",
-            "n": w.n, "m": w.m, "input_clusters": w.n_clusters, "min_size": MIN_SIZE,
+def n_clusters(w) -> int:
+    return int(w.meta["clusters"]) if w.meta and "clusters" in w.meta else int(w.n_clusters)
+
+
+def describe(name: str, w) -> dict:
+    text = {
+        "lfr_100k": f"LFR-style graph, {w.n} vertices, {w.m} undirected edges, {n_clusters(w)} input "
+                    "clusters (10% merged pairwise by 1-2 bridges)",
+        "planted_1k": f"planted partition, {w.n} vertices, {w.m} edges, 20 blocks of 50 (4 bridged "
+                      "halves, 10 pendant vertices)",
+        "dcpp_10m": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected edges, "
+                    f"{n_clusters(w)} clusters (sizes 10-50,000, 5% chains of 2-4 parts)",
+        "dcpp_100m": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected edges, "
+                     f"{n_clusters(w)} clusters (sizes 10-100,000, 3% bridged two-part clusters)",
+    }[name]
+    return {"workload": f"{name}: {text}, criterion floor(log10 n), min size {w.min_size}",
+            "n": int(w.n), "m": int(w.m), "input_clusters": n_clusters(w), "min_size": int(w.min_size),
             "rule": "log10", "l2": "flushed before every timed step (512 MiB device write)"}
 
 
@@ -134,24 +165,58 @@ def oracle_step(w):
     return out
 
 
-def cpu_baseline(w, budget_s: float = 12.0):
-    """The oracle as it stands, single-threaded, repeated on the full workload
-    until ~budget_s of CPU time: edges/s."""
+def cluster_sample(w, max_edges: int = 1_500_000, seed: int = 0):
+    """A seeded sample of whole input clusters of a large device-generated
+    workload, as a small host workload: the subgraph they induce, with vertex
+    ids renumbered monotonically (refinement depends only on each cluster's
+    induced subgraph, and a monotone renumbering keeps every tie-break)."""
+    import numpy as np
+    import torch
+    import synth
+    rng = np.random.default_rng(seed)
+    lab_of = w.meta["label_of_cluster"]
+    sizes = w.meta["cluster_sizes"]
+    order = rng.permutation(len(sizes))
+    # about max_edges / mean intra-degree vertices' worth of clusters
+    deg = 2.0 * w.m / w.n
+    budget_v = max_edges / max(deg * 0.4, 1.0)
+    take = order[np.cumsum(sizes[order]) <= budget_v]
+    sample = torch.from_numpy(np.unique(lab_of[take]).astype(np.int32)).to(w.labels.device)
+    in_s = torch.isin(w.labels, sample)
+    ids = torch.nonzero(in_s).flatten()
+    keep = in_s[w.src.long()] & in_s[w.dst.long()] & (w.labels[w.src.long()] == w.labels[w.dst.long()])
+    su = torch.searchsorted(ids, w.src[keep].long()).to(torch.int32).cpu().numpy()
+    sv = torch.searchsorted(ids, w.dst[keep].long()).to(torch.int32).cpu().numpy()
+    lab = w.labels[ids].cpu().numpy()
+    s = synth.Workload("sample", int(ids.numel()), su, sv, lab, int(w.min_size))
+    return s, int(sample.numel())
+
+
+def cpu_baseline(name, w, budget_s: float = 12.0):
+    """The oracle as it stands, single-threaded, repeated until ~budget_s of
+    CPU time: edges/s.  Small workloads run in full; large ones on a seeded
+    sample of whole input clusters."""
     import oracle
     oracle.build()
+    if name in LARGE:
+        sw, k = cluster_sample(w)
+        what = f"{k} whole input clusters of {name} sampled ({sw.n} vertices, {sw.m} intra-cluster edges)"
+    else:
+        sw, k = w, n_clusters(w)
+        what = f"the full {name} workload"
     times = []
     t_all = time.perf_counter()
     while True:
         t0 = time.perf_counter()
-        oracle_step(w)
+        oracle_step(sw)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_all > budget_s or len(times) >= 50:
             break
     mean = sum(times) / len(times)
-    return {"value": w.m / mean, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"the full {WORKLOAD} workload (CSR build + refinement), "
-                      f"{len(times)} repetitions, mean {mean * 1e3:.1f} ms each",
-            "clusters_per_s": w.n_clusters / mean}
+    return {"value": sw.m / mean, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{what} (CSR build + refinement), {len(times)} repetitions, "
+                      f"mean {mean * 1e3:.1f} ms each",
+            "clusters_per_s": k / mean}
 
 
 def run_reference(args):
@@ -160,24 +225,30 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    w = workload(0)
+    w = workload(args.workload, 0)
+    if args.workload in LARGE:
+        sw, k = cluster_sample(w)
+        what = f"{k} whole input clusters of {args.workload} per step ({sw.m} intra-cluster edges)"
+    else:
+        sw, k = w, n_clusters(w)
+        what = f"the full {args.workload} workload per step"
     for _ in range(args.warmup):
-        oracle_step(w)
+        oracle_step(sw)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle_step(w)
+        oracle_step(sw)
         times.append(time.perf_counter() - t0)
     total = sum(times)
-    value = w.m * args.steps / total
+    value = sw.m * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": describe(w),
-            "clusters_per_s": w.n_clusters * args.steps / total,
+            "config": describe(args.workload, w),
+            "clusters_per_s": k * args.steps / total,
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"the full {WORKLOAD} workload per step"},
+                             "sample": what},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -285,8 +356,10 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="lfr_100k", choices=WORKLOADS)
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--resident-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=240)
     args = ap.parse_args()
@@ -314,14 +387,16 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = workload(rank)
+    name = args.workload
+    large = name in LARGE
+    w = workload(name, rank)
     dev = torch.device("cuda", local)
-    src_d = torch.from_numpy(w.src).to(dev)
-    dst_d = torch.from_numpy(w.dst).to(dev)
-    lab_d = torch.from_numpy(w.labels).to(dev)
+    as_dev = (lambda x: x.to(dev)) if torch.is_tensor(w.src) else (lambda x: torch.from_numpy(x).to(dev))
+    src_d, dst_d, lab_d = as_dev(w.src), as_dev(w.dst), as_dev(w.labels)
     out_d = torch.empty_like(lab_d)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    k_in = n_clusters(w)
 
     def step(mode="batched"):
         g = wcc.WccGraph.from_edges(src_d, dst_d, w.n)
@@ -333,7 +408,6 @@ def main():
 
     for _ in range(args.warmup):
         step()
-    # correctness guard on rank 0 (outside the timed region)
     barrier()
 
     sampler = ClockSampler(local)
@@ -357,16 +431,44 @@ def main():
     sampler.stop()
     clocks = sampler.summary(t_begin, t_end)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms, m_all, k_all = aggregate_ranks(dist, torch, dev, sum(step_ms), w.m, w.n_clusters)
+    total_ms, m_all, k_all = aggregate_ranks(dist, torch, dev, sum(step_ms), w.m, k_in)
     value = m_all * args.steps / (total_ms / 1e3)
     clusters_per_s = k_all * args.steps / (total_ms / 1e3)
-    srt = sorted(step_ms)
-    p50 = srt[len(srt) // 2]
-    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+    # the refinement alone on a resident graph, and the CSR build alone
+    csr_ms, res_ms = [], []
+    g_res = None
+    for k in range(max(args.resident_steps, 0) + 2 if args.resident_steps > 0 else 0):
+        flush.fill_(k & 0xff)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        if g_res is None:
+            g_res = wcc.WccGraph.from_edges(src_d, dst_d, w.n)
+            b.record(stream)
+        else:
+            b.record(stream)
+        g_res.run(lab_d, min_size=w.min_size, out=out_d)
+        c.record(stream)
+        torch.cuda.synchronize()
+        if k == 0:
+            csr_ms.append(a.elapsed_time(b))
+        elif k >= 2:
+            res_ms.append(b.elapsed_time(c))
+    resident = None
+    if res_ms:
+        rm = sum(res_ms) / len(res_ms)
+        resident = {"edges_per_s": w.m / (rm / 1e3), "clusters_per_s": k_in / (rm / 1e3),
+                    "ms_per_run": rm, "p50_ms": pct(res_ms, 0.5), "p99_ms": pct(res_ms, 0.99),
+                    "runs": len(res_ms), "csr_build_ms": csr_ms[0] if csr_ms else None}
+        g_res.close()
 
     # plain path (one kernel launch per work item), same workload
     plain = None
-    if args.plain_steps > 0:
+    if args.plain_steps > 0 and not large:
         pms = []
         for k in range(args.plain_steps):
             flush.fill_(k & 0xff)
@@ -377,16 +479,18 @@ def main():
             torch.cuda.synchronize()
             pms.append(a.elapsed_time(b))
         pm = sum(pms) / len(pms)
-        plain = {"edges_per_s": w.m / (pm / 1e3), "clusters_per_s": w.n_clusters / (pm / 1e3),
+        plain = {"edges_per_s": w.m / (pm / 1e3), "clusters_per_s": k_in / (pm / 1e3),
                  "ms_per_step": pm, "steps": len(pms)}
+    ref_out = out_d.clone()
 
     # end to end through the public API with pinned host buffers
-    src_h = torch.from_numpy(w.src).pin_memory()
-    dst_h = torch.from_numpy(w.dst).pin_memory()
-    lab_h = torch.from_numpy(w.labels).pin_memory()
+    src_h = src_d.cpu().pin_memory()
+    dst_h = dst_d.cpu().pin_memory()
+    lab_h = lab_d.cpu().pin_memory()
     out_h = torch.empty_like(lab_h).pin_memory()
+    e2e_steps = min(args.e2e_steps, 2) if large else args.e2e_steps
     e2e_t = []
-    for k in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 1):
+    for k in range(e2e_steps + 2 if e2e_steps > 0 else 1):
         flush.fill_(k & 0xff)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -400,7 +504,7 @@ def main():
         dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
     e2e_value = m_all / float(e2e_local.item())
     # the result must match the device-buffer run
-    ok = bool(np.array_equal(out_h.numpy(), out_d.cpu().numpy()))
+    ok = bool(torch.equal(out_h, ref_out.cpu()))
 
     # roofline of the dominant kernel (the refinement kernel)
     peak, peak_kind = hbm_peak()
@@ -411,10 +515,11 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": peak_kind, "alg_bytes_per_launch": r_bytes,
                 "ms_per_launch": r_ms, "share_of_step": r_ms / (total_ms / args.steps)}
-    roofline["traffic"] = profiled_traffic()
+    if name == "lfr_100k":
+        roofline["traffic"] = profiled_traffic()
 
     serving = None
-    if args.serving_requests > 0:
+    if args.serving_requests > 0 and name == "lfr_100k":
         serving = serving_bench(wcc, np, torch, n_requests=args.serving_requests, seed=rank)
 
     if rank == 0:
@@ -422,18 +527,20 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": describe(w) | {"mode": "batched", "parallelism": f"independent x{world}"},
-                "clusters_per_s": clusters_per_s, "p50_ms": p50, "p99_ms": p99,
+                "config": describe(name, w) | {"mode": "batched", "parallelism": f"independent x{world}"},
+                "clusters_per_s": clusters_per_s, "p50_ms": pct(step_ms, 0.5),
+                "p99_ms": pct(step_ms, 0.99),
+                "graph_resident": resident,
                 "plain": plain,
                 "batched_over_plain": (value / (plain["edges_per_s"] * world)) if plain else None,
                 "e2e": {"value": e2e_value, "unit": "edges/s",
                         "h2d_bytes_per_step": int(8 * w.m + 4 * w.n),
                         "d2h_bytes_per_step": int(4 * w.n), "ms_per_step": 1e3 * e2e_mean,
-                        "matches_device_run": ok},
+                        "steps": len(e2e_t), "matches_device_run": ok},
                 "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
                 "serving": serving}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(name, w)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
