@@ -114,7 +114,7 @@ struct RunCounters {
   unsigned int error;          // DERR_* bits
   unsigned int err_info;       // first failing detail (debug aid)
   int open;                    // 1 while a server may still add work (kernel idles instead of exiting)
-  int pad;
+  int closing;                 // set by the first CTA of an open kernel that idled out: all leave
 };
 
 // Optional per-item profile record (phase durations in SM cycles: load,

@@ -1881,8 +1881,9 @@ __device__ int run_item(const RefineParams &P, unsigned long long seq, const Ite
 // tail), by compare-and-swap, and then waits -- bounded by wait_limit_ns --
 // for its publication.  With nothing reserved it waits for more: the kernel
 // ends when nothing is pending and the queue is closed, or (open, serving)
-// when nothing has been pending for idle_limit_ns; a wait for work that is
-// pending but never published ends at wait_limit_ns with DERR_TIMEOUT.
+// once one CTA has found nothing pending for idle_limit_ns and set closing;
+// a wait for work that is pending but never published ends at wait_limit_ns
+// with DERR_TIMEOUT.
 __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
   __shared__ Sh sh;
   char *slab = P.slab + (size_t)blockIdx.x * P.slab_bytes;
@@ -1910,10 +1911,18 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
           }
           continue;
         }
+        // an open (serving) kernel leaves as a whole: the first CTA that
+        // idled out closes it for all, so that work admitted meanwhile never
+        // runs on a few stragglers; the host relaunches it for that work
+        if (vctr->closing) break;
         const long long pend = vctr->pending;
         const uint64_t waited = globaltimer_ns() - t0;
         if (pend <= 0) {
-          if (!vctr->open || waited > P.idle_limit_ns) break;
+          if (!vctr->open) break;
+          if (waited > P.idle_limit_ns) {
+            atomicExch(&ctr->closing, 1);
+            break;
+          }
         } else if (waited > P.wait_limit_ns) {
           atomicOr(&ctr->error, DERR_TIMEOUT);
           break;

@@ -16,7 +16,8 @@
 //     releases its memory;
 //   - relaunches the kernel whenever it has gone idle and work is pending.
 // The kernel runs with its queue "open": with nothing pending it waits
-// (bounded by an idle limit) instead of exiting.
+// (bounded by an idle limit) instead of exiting, and when it does leave, it
+// leaves as a whole (no CTA keeps running alone on work admitted late).
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -225,6 +226,8 @@ void launch_kernel(Server *S) {
   p.dense_max = dense_max_config();
   p.slab = S->slab.as<char>();
   p.slab_bytes = S->slab_bytes;
+  // a previous instance may have closed on idling out; the launch reopens
+  WCC_CUDA(cudaMemsetAsync(&S->ctr.as<RunCounters>()->closing, 0, sizeof(int), S->kstream));
   launch_refine(p, S->grid, true, S->kstream);
   WCC_CUDA(cudaEventRecord(S->kdone, S->kstream));
   S->kernel_running = true;
