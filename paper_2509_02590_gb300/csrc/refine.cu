@@ -790,7 +790,7 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
   const int W = m.W, S = m.S;
   const bool summaries = W > 64;
   uint32_t *vis_w = reinterpret_cast<uint32_t *>(m.E);
-  int32_t *pos = m.F, *sat = m.H;
+  int32_t *pos = m.F, *sat = m.H, *ord = m.D;
   uint32_t *sink = sh.sink;  // per-lane dummy targets
   for (int i = threadIdx.x; i < n; i += RB) {
     m.kst[i] = m.alive[i] ? 0 : 255;
@@ -832,6 +832,7 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
           break;
         }
         pos[X] = step;
+        ord[step] = X;
         kst[X] = 255;
         const int xw = X >> 5;
         const uint32_t xb = 1u << (X & 31);
@@ -901,6 +902,7 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
         break;
       }
       pos[X] = step;
+      ord[step] = X;
       kst[X] = 255;
       if (!summaries) {
         const int xw = X >> 5;
@@ -986,45 +988,74 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
   }
   __syncthreads();
   const long long tm0 = P.prof ? clock64() : 0;
-  // merge the ends of every entry a -> j whose key reached kcap while j was
-  // still unadded (union-find, root = smallest id); rows longer than 32
-  // entries are listed for whole warps
+  // Merge the ends of every entry a -> j whose key reached kcap while j was
+  // still unadded (union-find, root = smallest id), Afforest-style: a vertex
+  // whose key reached kcap did so when the vertex added at that step
+  // (ord[sat]) scanned it, and that pair is one such entry, so one union per
+  // vertex builds most of the structure; then only vertices outside the
+  // largest set so formed scan their rows (an edge with both ends inside it
+  // adds nothing, and an edge with one end outside is seen from that end).
+  // Rows longer than 32 entries are listed for whole warps.
   int32_t *lr = m.C;
+  uint8_t *out_g = m.flag;
   for (int i = threadIdx.x; i < n; i += RB) nrep[i] = i;
   if (threadIdx.x == 0) sh.ntouched = 0;
   __syncthreads();
   int any = 0;
-  for (int a = threadIdx.x; a < n; a += RB) {
-    if (!m.alive[a]) continue;
-    const int b0 = m.off[a], e0 = m.off[a + 1];
+  for (int i = threadIdx.x; i < n; i += RB) {
+    const int si = sat[i];
+    if (si < nsv && m.alive[i]) {
+      uf_union(nrep, i, ord[si]);
+      any = 1;
+    }
+  }
+  if (!__syncthreads_or(any)) return false;  // no key reached kcap: nothing merges
+  for (int i = threadIdx.x; i < n; i += RB)
+    if (m.alive[i]) nrep[i] = uf_find(nrep, i);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // the root held by most of 32 spread vertices
+    const int lane = threadIdx.x;
+    const int v = (int)(((long long)lane * n) / 32);
+    const int r = m.alive[v] ? nrep[v] : -1;
+    const unsigned peers = __match_any_sync(FULL, r);
+    const unsigned long long key =
+        r >= 0 ? ((unsigned long long)__popc(peers) << 32) | (unsigned)r : 0ull;
+    const unsigned long long best = warp_max(key);
+    if (lane == 0) sh.i0 = best ? (int)(best & 0xffffffffu) : -1;
+  }
+  __syncthreads();
+  const int giant = sh.i0;
+  for (int i = threadIdx.x; i < n; i += RB) out_g[i] = m.alive[i] && nrep[i] != giant;
+  __syncthreads();
+  auto marked = [&](int v, int u) {  // the edge {v, u} is contracted
+    const int pv = pos[v], pu = pos[u];
+    return pv < pu ? sat[u] <= pv : sat[v] <= pu;
+  };
+  for (int v = threadIdx.x; v < n; v += RB) {
+    if (!out_g[v]) continue;
+    const int b0 = m.off[v], e0 = m.off[v + 1];
     if (e0 - b0 > 32) {
-      lr[atomicAdd(&sh.ntouched, 1)] = a;
+      lr[atomicAdd(&sh.ntouched, 1)] = v;
       continue;
     }
-    const int pa = pos[a];
     for (int q = b0; q < e0; ++q) {
-      const int j = m.adj[q];
-      if (sat[j] <= pa && pa < pos[j]) {  // sat[j] <= pa implies j is alive
-        uf_union(nrep, a, j);
-        any = 1;
-      }
+      const int u = m.adj[q];
+      if (m.alive[u] && marked(v, u)) uf_union(nrep, v, u);
     }
   }
   __syncthreads();
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nlr = sh.ntouched;
     for (int k = warp; k < nlr; k += RW) {
-      const int a = lr[k], pa = pos[a];
-      for (int q = m.off[a] + lane; q < m.off[a + 1]; q += 32) {
-        const int j = m.adj[q];
-        if (sat[j] <= pa && pa < pos[j]) {
-          uf_union(nrep, a, j);
-          any = 1;
-        }
+      const int v = lr[k];
+      for (int q = m.off[v] + lane; q < m.off[v + 1]; q += 32) {
+        const int u = m.adj[q];
+        if (m.alive[u] && marked(v, u)) uf_union(nrep, v, u);
       }
     }
   }
-  if (!__syncthreads_or(any)) return false;
+  __syncthreads();
   for (int i = threadIdx.x; i < n; i += RB)
     if (m.alive[i]) nrep[i] = uf_find(nrep, i);
   __syncthreads();
