@@ -79,7 +79,8 @@ struct Mem {
   int64_t *wide;       // E..F viewed as int64[n+1]
   uint8_t *alive, *flag, *side;
   uint8_t *kst;        // first contraction pass: capped key, or 255 once added / dead
-  uint32_t *bm, *bms;  // bucket bitmaps [KB_LEVELS][W], summaries [KB_LEVELS][S]
+  uint32_t *bm, *bms;  // bucket bitmaps [levels][W], summaries [levels][S]
+  uint32_t *vis;       // first contraction pass: added vertices, one bit each (W words)
   int W, S;
   uint32_t *ebits;     // one bit per local adjacency entry
   IT *adj;
@@ -111,7 +112,35 @@ __device__ __forceinline__ Mem<IT> carve(char *base, int n, int64_t d) {
   m.bms = m.bm + (size_t)KB_LEVELS * m.W;
   m.ebits = (uint32_t *)take(4 * (size_t)((d + 31) / 32 + 1));
   m.adj = (IT *)take(sizeof(IT) * (size_t)d);
+  m.vis = reinterpret_cast<uint32_t *>(m.E);
   return m;
+}
+
+// An item in the global slab keeps the first contraction pass's hot state --
+// keys (n bytes), the key levels it can use with their summaries, the added
+// bits -- in shared memory when that fits: the pass's dependent chain then
+// never waits on L2.  levels = T(n)+2 bounds kcap+1, since the peel only
+// lowers n.
+__host__ __device__ inline size_t hot_bytes(int64_t n, int levels) {
+  return align16((size_t)n) + align16(4 * (size_t)levels * (size_t)(bm_words(n) + bm_sum_words(n))) +
+         align16(4 * (size_t)bm_words(n));
+}
+// Also the local row offsets (read on every step's dependent chain) when
+// they fit beside the rest.
+template <typename IT>
+__device__ __forceinline__ bool carve_hot(Mem<IT> &m, int n, int levels, size_t smem_bytes) {
+  const size_t hb = hot_bytes(n, levels);
+  if (hb > smem_bytes) return false;
+  char *h = wcc_dyn_smem;
+  m.kst = reinterpret_cast<uint8_t *>(h);
+  h += align16((size_t)n);
+  m.bm = reinterpret_cast<uint32_t *>(h);
+  m.bms = m.bm + (size_t)levels * m.W;
+  h += align16(4 * (size_t)levels * (size_t)(m.W + m.S));
+  m.vis = reinterpret_cast<uint32_t *>(h);
+  h += align16(4 * (size_t)m.W);
+  if (hb + align16(4 * (size_t)(n + 1)) <= smem_bytes) m.off = reinterpret_cast<int32_t *>(h);
+  return true;
 }
 
 // Block-level scalars.
@@ -765,7 +794,7 @@ __device__ __forceinline__ int next_member(volatile uint32_t *bm, volatile uint3
 //
 // A key grows by exactly one per step, so the key levels are cumulative
 // bitmaps (bit v of level L is set once v's key reaches L) and added
-// vertices are masked out by the vis bitmap (E; in registers, lane l holding
+// vertices are masked out by the vis bitmap (in registers, lane l holding
 // words l and l+32, when a level has at most 64 words).  With top = the
 // largest key of an unadded vertex, the added vertex X is always the
 // smallest unadded member of level top, so the next pick is one of: the
@@ -779,17 +808,18 @@ __device__ __forceinline__ int next_member(volatile uint32_t *bm, volatile uint3
 // The step records only when each vertex was added (pos, F) and when each
 // key reached kcap (sat, H); the entry X -> j is contracted iff j was still
 // unadded when X was added and its key had reached kcap by then, which the
-// whole block evaluates afterwards into one bit per adjacency entry.  The
-// step is written without lane-divergent branches: lanes without work
-// write to per-lane dummy words or store the value every lane stores.  Returns whether anything merged; nrep receives
-// the merged sets labelled by their smallest id.
+// whole block evaluates afterwards, merging the ends by union-find.  The
+// step is written without lane-divergent branches: lanes without work write
+// to per-lane dummy words or store the value every lane stores.  Returns
+// whether anything merged; nrep receives the merged sets labelled by their
+// smallest id.
 template <typename IT>
 __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<IT> &m, int32_t *nrep,
                                               int n, int nsv, int kcap, int E, unsigned *err,
                                               Sh &sh) {
   const int W = m.W, S = m.S;
   const bool summaries = W > 64;
-  uint32_t *vis_w = reinterpret_cast<uint32_t *>(m.E);
+  uint32_t *vis_w = m.vis;
   int32_t *pos = m.F, *sat = m.H, *ord = m.D;
   uint32_t *sink = sh.sink;  // per-lane dummy targets
   for (int i = threadIdx.x; i < n; i += RB) {
@@ -896,90 +926,101 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
         __syncwarp();
       }
     } else {
-    for (int step = 0; step < nsv; ++step) {
-      if (X < 0) {
-        if (lane == 0) atomicOr(err, DERR_INTERNAL);
-        break;
-      }
-      pos[X] = step;
-      ord[step] = X;
-      kst[X] = 255;
-      if (!summaries) {
-        const int xw = X >> 5;
-        const uint32_t xb = 1u << (X & 31);
-        va |= xw == lane ? xb : 0u;
-        vb |= xw == lane + 32 ? xb : 0u;
-      } else {
+      // levels of more than 64 words: the successor is looked for in the 64
+      // words from X's on (nearly always there in a dense level), else
+      // through the summary bits; added bits are in vis.  The successor is
+      // the next vertex about two times in three, so its row bounds and
+      // first adjacency chunk are loaded speculatively during the step
+      // (rows may sit in the global slab, where each dependent load costs
+      // an L2 round trip).
+      int pf_x = -1, pf_b = 0, pf_e = 0, pf_j = 0;
+      for (int step = 0; step < nsv; ++step) {
+        if (X < 0) {
+          if (lane == 0) atomicOr(err, DERR_INTERNAL);
+          break;
+        }
+        pos[X] = step;
+        ord[step] = X;
+        kst[X] = 255;
         atomicOr(lane == 0 ? &vis_w[X >> 5] : &sink[lane], lane == 0 ? 1u << (X & 31) : 0u);
-      }
-      if (step == nsv - 1) break;
-      int succ;
-      const int b = m.off[X], e = m.off[X + 1];
-      int j0, ok0;
-      if (!summaries) {
-        // issue the successor's loads and the first neighbour loads before
-        // any of them is used, so that their latencies overlap
-        const int wt = top * W;
-        const uint32_t sa = lane < W ? bm[wt + lane] : 0u;
-        const uint32_t sb = lane + 32 < W ? bm[wt + 32 + lane] : 0u;
-        j0 = b + lane < e ? (int)m.adj[b + lane] : X;
+        {
+          // keep the summaries exact: lane L drops X's word from level L's
+          // summary when X was its last unadded member there (before this
+          // step's key updates, which set any bit they need again)
+          const int xw = X >> 5;
+          const uint32_t left = lane <= top ? (uint32_t)bm[lane * W + xw] & ~((uint32_t)vis[xw] | (1u << (X & 31))) : 1u;
+          atomicAnd(left == 0u ? (uint32_t *)&bms[lane * S + (xw >> 5)] : &sink[lane],
+                    left == 0u ? ~(1u << (xw & 31)) : 0xffffffffu);
+        }
+        if (step == nsv - 1) break;
+        const bool hit = X == pf_x;
+        const int b = hit ? pf_b : m.off[X], e = hit ? pf_e : m.off[X + 1];
         const int p1 = X + 1, w1 = p1 >> 5;
-        const uint32_t fm = 0xffffffffu << (p1 & 31);
-        uint32_t a = lane >= w1 ? sa & ~va : 0u;
-        uint32_t c = lane + 32 >= w1 ? sb & ~vb : 0u;
-        a &= lane == w1 ? fm : 0xffffffffu;
-        c &= lane + 32 == w1 ? fm : 0xffffffffu;
-        ok0 = kst[j0];
-        const unsigned ba = __ballot_sync(FULL, a != 0u), bc = __ballot_sync(FULL, c != 0u);
-        const int fl = ba ? __ffs(ba) - 1 : 32 + __ffs(bc) - 1;
-        const uint32_t word = __shfl_sync(FULL, fl < 32 ? a : c, fl & 31);
-        succ = (ba | bc) ? fl * 32 + __ffs(word) - 1 : -1;
-      } else {
-        succ = next_member(bm, bms, vis, W, S, top, X, false);
-        j0 = b + lane < e ? (int)m.adj[b + lane] : X;
-        ok0 = kst[j0];
-      }
-      unsigned best = 0u;  // (new key << 24) | (0xffffff - id) of the moved neighbours
-      for (int q0 = b; q0 < e; q0 += 32) {
-        const int q = q0 + lane;
-        const int j = q0 == b ? j0 : (q < e ? (int)m.adj[q] : X);
-        const int ok = q0 == b ? ok0 : (int)kst[j];
-        const int nk = ok + 1 < kcap ? ok + 1 : kcap;
-        const bool moved = ok != 255 && nk != ok;
+        const int ia = w1 + lane, ib = w1 + 32 + lane;
+        const uint32_t sa = ia < W ? bm[top * W + ia] : 0u, sb = ib < W ? bm[top * W + ib] : 0u;
+        const uint32_t va = ia < W ? (uint32_t)vis[ia] : 0xffffffffu;
+        const uint32_t vb = ib < W ? (uint32_t)vis[ib] : 0xffffffffu;
+        const int q = b + lane;
+        const int jr = hit ? pf_j : (int)m.adj[q < e ? q : b];
+        const int j = q < e ? jr : X;
+        uint32_t wa = sa & ~va;
+        const uint32_t wb = sb & ~vb;
+        wa &= lane == 0 ? 0xffffffffu << (p1 & 31) : 0xffffffffu;
+        const int ok = kst[j];
+        const unsigned ba = __ballot_sync(FULL, wa != 0u), bb = __ballot_sync(FULL, wb != 0u);
+        int succ;
+        if (ba | bb) {
+          const int fl = ba ? __ffs(ba) - 1 : 32 + __ffs(bb) - 1;
+          const uint32_t word = __shfl_sync(FULL, fl < 32 ? wa : wb, fl & 31);
+          succ = (w1 + fl) * 32 + __ffs(word) - 1;
+        } else {
+          succ = w1 + 64 < W ? next_member(bm, bms, vis, W, S, top, 32 * (w1 + 64) - 1, false) : -1;
+        }
+        const unsigned ks = succ >= 0 ? ((unsigned)top << 24) | (0xffffffu - (unsigned)succ) : 0u;
+        // speculative row bounds of the successor (used next step if it is picked)
+        const int nb = succ >= 0 ? m.off[succ] : 0, ne = succ >= 0 ? m.off[succ + 1] : 0;
+        const bool moved = ok < kcap;
+        const int nk = ok + 1;
         kst[moved ? j : X] = moved ? (uint8_t)nk : (uint8_t)255;
         atomicOr(moved ? &m.bm[nk * W + (j >> 5)] : &sink[lane], moved ? 1u << (j & 31) : 0u);
-        if (summaries)
-          atomicOr(moved ? &m.bms[nk * S + (j >> 10)] : &sink[lane],
-                   moved ? 1u << ((j >> 5) & 31) : 0u);
-        sat[moved && nk >= kcap ? j : n] = step;  // H[n] is spare
-        const unsigned pk = ((unsigned)nk << 24) | (0xffffffu - (unsigned)j);
-        best = moved && pk > best ? pk : best;
-      }
-      best = __reduce_max_sync(FULL, best);
-      const int mx = (int)(best >> 24);
-      const int arr = (int)(0xffffffu - (best & 0xffffffu));
-      if (best && mx > top) {
-        top = mx;
-        X = arr;
-      } else if (best && mx == top) {
-        X = succ < 0 ? arr : (succ < arr ? succ : arr);
-      } else if (succ >= 0) {
-        X = succ;
-      } else {
-        // level top has no unadded member left: the highest level that has
-        if (!summaries) {
-          if (lane < W) vis[lane] = va;
-          if (lane + 32 < W) vis[32 + lane] = vb;
+        atomicOr(moved ? &m.bms[nk * S + (j >> 10)] : &sink[lane], moved ? 1u << ((j >> 5) & 31) : 0u);
+        sat[moved && nk == kcap ? j : n] = step;
+        unsigned pk = moved ? ((unsigned)nk << 24) | (0xffffffu - (unsigned)j) : 0u;
+        pk = pk > ks ? pk : ks;
+        for (int q0 = b + 32; q0 < e; q0 += 32) {  // rows longer than 32 entries
+          const int qq = q0 + lane;
+          const int jj = qq < e ? (int)m.adj[qq] : X;
+          const int o2 = kst[jj];
+          const bool mv2 = o2 < kcap;
+          const int n2 = o2 + 1;
+          kst[mv2 ? jj : X] = mv2 ? (uint8_t)n2 : (uint8_t)255;
+          atomicOr(mv2 ? &m.bm[n2 * W + (jj >> 5)] : &sink[lane], mv2 ? 1u << (jj & 31) : 0u);
+          atomicOr(mv2 ? &m.bms[n2 * S + (jj >> 10)] : &sink[lane], mv2 ? 1u << ((jj >> 5) & 31) : 0u);
+          sat[mv2 && n2 == kcap ? jj : n] = step;
+          const unsigned p2 = mv2 ? ((unsigned)n2 << 24) | (0xffffffu - (unsigned)jj) : 0u;
+          pk = p2 > pk ? p2 : pk;
+        }
+        // the successor's first adjacency chunk, issued after this step's own
+        // loads so that waiting for its row bounds stalls nothing
+        pf_x = succ;
+        pf_b = nb;
+        pf_e = ne;
+        pf_j = succ >= 0 ? (int)m.adj[nb + lane < ne ? nb + lane : nb] : 0;
+        pk = __reduce_max_sync(FULL, pk);
+        if (pk != 0u && (int)(pk >> 24) >= top) {
+          top = (int)(pk >> 24);
+          X = (int)(0xffffffu - (pk & 0xffffffu));
+        } else {
+          // level top has no unadded member left: the highest level that has
+          __syncwarp();
+          X = -1;
+          while (top > 0 && X < 0) {
+            --top;
+            X = next_member(bm, bms, vis, W, S, top, -1, true);
+          }
         }
         __syncwarp();
-        X = -1;
-        while (top > 0 && X < 0) {
-          --top;
-          X = next_member(bm, bms, vis, W, S, top, -1, true);
-        }
       }
-      __syncwarp();
-    }
     }
     if (lane == 0) {
       sh.dbg[0] = P.prof ? clock64() - tp0 : 0;
@@ -1539,6 +1580,10 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   const ReqCtx R = load_ctx(Rg);
   ReqCtx *ctr = Rg;  // per-request statistics (atomics)
   Mem<IT> m = carve<IT>(base, n, dbound);
+  if (!SM) {
+    const int64_t T0 = threshold_of(R.rule_kind, R.rule_num, R.rule_den, n);
+    carve_hot(m, n, (int)(T0 + 2 < KB_LEVELS ? T0 + 2 : KB_LEVELS), P.smem_bytes);
+  }
 
   // global row start and degree of every member
   int64_t *gbeg = m.wide;
