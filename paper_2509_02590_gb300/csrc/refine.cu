@@ -1607,7 +1607,38 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   // its neighbour u iff slot[u] names this item; tmp[f] = local id or ~0
   IT *tmp = m.adj;
   const IT NONE = (IT)~(IT)0;
-  {
+  if (!SM) {
+    // items in the global slab: their row bounds are global too, so a
+    // per-entry row cursor would put a dependent global load on every
+    // entry; instead each warp takes two rows at a time, reads their bounds
+    // once, and its lanes walk the rows together (64 neighbour loads and 64
+    // slot gathers in flight per warp)
+    for (int r0 = 2 * warp; r0 < n; r0 += 2 * RW) {
+      const int r1 = r0 + 1 < n ? r0 + 1 : r0;
+      const int o0 = pdeg[r0], d0 = pdeg[r0 + 1] - o0;
+      const int o1 = pdeg[r1], d1 = r1 != r0 ? pdeg[r1 + 1] - o1 : 0;
+      const int64_t g0 = gbeg[r0], g1 = gbeg[r1];
+      int c0 = 0, c1 = 0;
+      const int dm = d0 > d1 ? d0 : d1;
+      for (int k = lane; k - lane < dm; k += 32) {
+        const bool a0 = k < d0, a1 = k < d1;
+        const int32_t u0 = a0 ? R.adj[g0 + k] : 0;
+        const int32_t u1 = a1 ? R.adj[g1 + k] : 0;
+        const unsigned long long s0 = a0 ? __ldcg(&R.slot[u0]) : 0ull;
+        const unsigned long long s1 = a1 ? __ldcg(&R.slot[u1]) : 0ull;
+        const bool h0 = a0 && (unsigned)(s0 >> 32) == queue_tag(seq);
+        const bool h1 = a1 && (unsigned)(s1 >> 32) == queue_tag(seq);
+        if (a0) tmp[o0 + k] = h0 ? (IT)(unsigned)(s0 & 0xffffffffu) : NONE;
+        if (a1) tmp[o1 + k] = h1 ? (IT)(unsigned)(s1 & 0xffffffffu) : NONE;
+        c0 += __popc(__ballot_sync(FULL, h0));
+        c1 += __popc(__ballot_sync(FULL, h1));
+      }
+      if (lane == 0) {
+        cnt[r0] = c0;
+        if (r1 != r0) cnt[r1] = c1;
+      }
+    }
+  } else {
     // warp w owns entries [w*chunk, (w+1)*chunk); lane l takes every 32nd
     // entry of it, four at a time, following its row with a cursor
     const int chunk = (D + RW - 1) / RW;
