@@ -145,6 +145,14 @@ int dense_max_config() {
   return (int)(v < 0 ? 0 : v > 32 ? 32 : v);
 }
 
+// Items of at most this many vertices (WCC_TINY_N, at most 32; 0 keeps every
+// item on a whole CTA) are refined one per warp, up to 8 at once per CTA.
+int tiny_max_config() {
+  const char *e = getenv("WCC_TINY_N");
+  long long v = e ? atoll(e) : 32;
+  return (int)(v < 0 ? 0 : v > 32 ? 32 : v);
+}
+
 // Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
 // largest a CTA can opt into, one CTA per SM).  Items whose working set is
 // larger use a global slab.
@@ -393,6 +401,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     p.slab_bytes = slab_bytes;
     p.forest_min_n = forest_min_n_config();
     p.dense_max = dense_max_config();
+    p.tiny_max = tiny_max_config();
     // optional per-item profile (WCC_PROFILE_ITEMS=<csv path>)
     const char *prof_path = getenv("WCC_PROFILE_ITEMS");
     DevBuf prof_buf;

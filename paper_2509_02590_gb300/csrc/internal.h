@@ -97,6 +97,7 @@ struct ReqCtx {
   int64_t rule_num, rule_den;
   long long pending;           // published but unfinished items of this request
   long long items, splits, peeled, ni_passes, sw_phases, accepted, alg_bytes;
+  unsigned long long seed_end; // end of the queue range of its input clusters (largest first)
 };
 
 // A ring slot: the item plus the queue sequence number it was published
@@ -145,6 +146,7 @@ struct RefineParams {
   size_t smem_bytes;          // dynamic shared memory per CTA
   int forest_min_n;           // smallest item that tries the forest acceptance test (0 = never)
   int dense_max;              // most super-vertices the dense finish takes (0 = never)
+  int tiny_max;               // items of at most this many vertices run one per warp (0 = never)
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
   ItemProf *prof;             // optional per-item profile (NULL = off)
@@ -202,6 +204,7 @@ uint64_t wait_limit_ns();                   // WCC_WAIT_LIMIT_MS (default 30 s)
 size_t refine_smem_bytes_config(int device);  // WCC_SMEM_KB (default: opt-in maximum)
 int forest_min_n_config();                    // WCC_FOREST_MIN_N
 int dense_max_config();                       // WCC_DENSE_NSV
+int tiny_max_config();                        // WCC_TINY_N
 wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule);
 
 template <typename T>

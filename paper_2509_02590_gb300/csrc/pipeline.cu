@@ -126,7 +126,9 @@ __global__ void k_reserve(RunCounters *ctr, ReqCtx *ctx, long long nkept,
     atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->pending),
               static_cast<unsigned long long>(nkept));
     __threadfence();
-    *base = atomicAdd(&ctr->tail, (unsigned long long)nkept);
+    const unsigned long long b = atomicAdd(&ctr->tail, (unsigned long long)nkept);
+    *base = b;
+    ctx->seed_end = b + (unsigned long long)nkept;
   }
 }
 

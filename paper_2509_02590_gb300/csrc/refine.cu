@@ -147,8 +147,6 @@ __device__ __forceinline__ bool carve_hot(Mem<IT> &m, int n, int levels, size_t 
 struct Sh {
   int32_t scan[RW + 1];
   long long lscan[RW + 1];
-  unsigned long long seq;
-  Item item;
   int go;
   int32_t i0;
   unsigned long long u0;
@@ -163,6 +161,9 @@ struct Sh {
   long long pf_forest_cycles, pf_t0;
   long long fdbg[6];
   uint32_t sink[32];  // per-lane dummy targets of branch-free warp code
+  Item batch[RW];     // claimed items: the first one, then more when it is tiny
+  unsigned long long bseq[RW];
+  int32_t nb;
   int32_t duf[32];    // dense finish: merges of one pass (union-find over indices)
   uint32_t dside;     // dense finish: side of the minimum cut (mask of indices)
   int32_t dcut, dpasses, dphases;
@@ -1500,27 +1501,32 @@ __device__ __forceinline__ void dense_order(const int32_t *w, int nsv, uint32_t 
   merged = __any_sync(FULL, merged);
 }
 
-// Runs the dense finish on w; fills sh.dside (side mask over the initial
-// indices, when the item fails), sh.dcut (the minimum cut, or -1 when the
-// contraction left one super-vertex: accept), sh.dpasses, sh.dphases.
-__device__ void dense_finish(int32_t *w, int nsv, int kcap, Sh &sh) {
-  if (threadIdx.x >= 32) return;
-  const int l = threadIdx.x;
-  uint32_t live = nsv >= 32 ? 0xffffffffu : (1u << nsv) - 1u;
+struct DenseResult {
+  int cut;        // minimum cut, or -1 when the contraction left one super-vertex
+  uint32_t side;  // the minimum cut's side (mask of initial indices)
+  int passes, phases;
+};
+
+// Runs the dense finish on w (nsv <= 32 indices; the super-vertices are the
+// indices in live0) with one warp (any warp; all its lanes call).  duf: 32
+// ints of scratch.  Every lane returns the result.
+__device__ DenseResult dense_finish(int32_t *w, int nsv, uint32_t live0, int kcap, int32_t *duf) {
+  const int l = threadIdx.x & 31;
+  uint32_t live = live0;
   uint32_t mem = 1u << l;  // lane l: the initial indices it holds
   int passes = 0, phases = 0;
   bool more = true;
   while (more && __popc(live) > 1) {
-    sh.duf[l] = l;
+    duf[l] = l;
     __syncwarp();
     int s, t, cut;
     bool merged;
-    dense_order(w, nsv, live, kcap, sh.duf, s, t, cut, merged);
+    dense_order(w, nsv, live, kcap, duf, s, t, cut, merged);
     ++passes;
     more = merged;
     if (!merged) break;
     // fold every merged index into its root, in ascending order
-    volatile int32_t *vd = sh.duf;
+    volatile int32_t *vd = duf;
     for (int x = 0; x < nsv; ++x) {
       if (!((live >> x) & 1u)) continue;
       int r = x;
@@ -1532,16 +1538,15 @@ __device__ void dense_finish(int32_t *w, int nsv, int kcap, Sh &sh) {
       live &= ~(1u << x);
     }
   }
-  int best = -1;
-  uint32_t side = 0u;
+  DenseResult res{-1, 0u, passes, 0};
   while (__popc(live) > 1) {
     int s, t, cut;
     bool merged;
-    dense_order(w, nsv, live, 0, sh.duf, s, t, cut, merged);
+    dense_order(w, nsv, live, 0, duf, s, t, cut, merged);
     ++phases;
-    if (best < 0 || cut < best) {
-      best = cut;
-      side = __shfl_sync(FULL, mem, t);
+    if (res.cut < 0 || cut < res.cut) {
+      res.cut = cut;
+      res.side = __shfl_sync(FULL, mem, t);
     }
     const int lo = s < t ? s : t, hi = s < t ? t : s;
     dense_fold(w, nsv, lo, hi);
@@ -1549,13 +1554,9 @@ __device__ void dense_finish(int32_t *w, int nsv, int kcap, Sh &sh) {
     if (l == lo) mem |= mh;
     live &= ~(1u << hi);
   }
-  if (l == 0) {
-    sh.dcut = best;
-    sh.dside = side;
-    sh.dpasses = passes;
-    sh.dphases = phases;
-  }
+  res.phases = phases;
   __syncwarp();
+  return res;
 }
 
 template <typename IT>
@@ -1566,6 +1567,220 @@ __device__ __forceinline__ void reset_ma_state(const Mem<IT> &m, int n) {
     m.flag[i] = 0;
   }
   __syncthreads();
+}
+
+// ---- items of at most 32 vertices: one warp each ---------------------------------
+// A CTA that claims such an item claims up to RW-1 more at once and gives
+// every tiny one to a warp of its own (larger ones run on the whole CTA
+// afterwards).  With n <= 32 the induced subgraph is a 32x32 bit matrix:
+// lane l holds member l's row as a bitmask over local ids, components grow
+// by OR-reductions of rows, the peel is a popcount, and the contraction
+// passes and Stoer-Wagner phases are the dense finish on the same matrix --
+// the same steps and rules as the CTA path, in registers.
+constexpr int TINY_MAX = 32;
+constexpr size_t TINY_SCRATCH = 4 * (32 * 32 + 32 + 32);  // weights, union-find, child masks
+
+__device__ __forceinline__ uint32_t tiny_component(uint32_t row, uint32_t set, int start) {
+  const int l = threadIdx.x & 31;
+  uint32_t V = 1u << start, F = V;
+  for (;;) {
+    const uint32_t nx = __reduce_or_sync(FULL, ((F >> l) & 1u) ? row : 0u) & set & ~V;
+    if (!nx) return V;
+    V |= nx;
+    F = nx;
+  }
+}
+
+// Queues every mask in cm[0..k) with at least min_size members as a child
+// item, written in place into the parent's pool range (one warp).
+__device__ void tiny_emit(const RefineParams &P, const ReqCtx &R, ReqCtx *Rg, const Item &it,
+                          int32_t v, const uint32_t *cm, int k) {
+  const int l = threadIdx.x & 31;
+  const uint32_t mine = l < k ? cm[l] : 0u;
+  const int size = __popc(mine);
+  const bool keep = l < k && size >= R.min_size;
+  const unsigned kept = __ballot_sync(FULL, keep);
+  const int nchild = __popc(kept);
+  if (nchild == 0) return;
+  const int off = warp_inclusive_scan(keep ? size : 0) - (keep ? size : 0);  // pool offset
+  unsigned long long s0 = 0;
+  if (l == 0) {
+    add_ll(&Rg->pending, (long long)nchild);
+    add_ll(&P.ctr->pending, (long long)nchild);
+    __threadfence();
+    s0 = atomicAdd(&P.ctr->tail, (unsigned long long)nchild);
+  }
+  s0 = __shfl_sync(FULL, s0, 0);
+  // member lanes: the kept child holding them
+  int c = -1;
+  for (int x = 0; x < k; ++x)
+    if (((kept >> x) & 1u) && ((cm[x] >> l) & 1u)) c = x;
+  const int coff = __shfl_sync(FULL, off, c < 0 ? 0 : c);
+  if (c >= 0) {
+    const int pos = __popc(cm[c] & ((1u << l) - 1u));
+    const unsigned long long q = s0 + __popc(kept & ((1u << c) - 1u));
+    R.pool[it.vbeg + coff + pos] = v;
+    R.slot[v] = ((unsigned long long)queue_tag(q) << 32) | (unsigned)pos;
+  }
+  __threadfence();
+  __syncwarp();
+  if (keep) {
+    const unsigned long long q = s0 + __popc(kept & ((1u << l) - 1u));
+    QSlot *sl = &P.ring[q % P.ring_cap];
+    sl->item.vbeg = it.vbeg + off;
+    sl->item.n = size;
+    sl->item.flags = 0;
+    sl->item.req = it.req;
+  }
+  __threadfence();
+  __syncwarp();
+  if (keep) {
+    const unsigned long long q = s0 + __popc(kept & ((1u << l) - 1u));
+    atomicExch((unsigned long long *)&P.ring[q % P.ring_cap].seq, q);
+  }
+}
+
+// Splits a set into its components (masks into cm); returns their count.
+__device__ __forceinline__ int tiny_components(uint32_t row, uint32_t set, uint32_t *cm) {
+  int k = 0;
+  uint32_t rem = set;
+  while (rem) {
+    const uint32_t c = tiny_component(row, set, __ffs(rem) - 1);
+    if ((threadIdx.x & 31) == 0) cm[k] = c;
+    ++k;
+    rem &= ~c;
+  }
+  __syncwarp();
+  return k;
+}
+
+constexpr int TINY_MAX_DEG = 1024;  // larger degree sums go to the whole CTA
+
+// Returns false, having done nothing, when the members' degree sum exceeds
+// TINY_MAX_DEG (a hub's row would keep one warp busy while its CTA waits).
+__device__ bool tiny_item(const RefineParams &P, unsigned long long seq, const Item &it,
+                          int32_t *scratch) {
+  const int l = threadIdx.x & 31;
+  const int n = it.n;
+  ReqCtx *Rg = &P.reqs[it.req];
+  const ReqCtx R = load_ctx(Rg);
+  int32_t *w = scratch, *duf = scratch + 32 * 32;
+  uint32_t *cm = reinterpret_cast<uint32_t *>(scratch + 32 * 32 + 32);
+  const bool mine = l < n;
+  const int32_t v = mine ? __ldcg(&R.pool[it.vbeg + l]) : -1;
+  const int64_t rb = mine ? R.off[v] : 0, re = mine ? R.off[v + 1] : 0;
+  const uint32_t tag = queue_tag(seq);
+  const int len = (int)(re - rb);
+  const long long D = warp_sum((long long)(mine ? len : 0));
+  if (D > TINY_MAX_DEG) return false;
+  // 1. extraction: rows of up to 64 entries by their own lane, four entries
+  // at a time; longer rows by the whole warp, one after the other
+  const bool shortrow = len <= 64;
+  uint32_t row = 0u;
+  const int wl = warp_max(shortrow ? len : 0);
+  for (int k = 0; k < wl; k += 4) {
+    int32_t u[4];
+    unsigned long long sl[4];
+#pragma unroll
+    for (int z = 0; z < 4; ++z) u[z] = (shortrow && k + z < len) ? R.adj[rb + k + z] : -1;
+#pragma unroll
+    for (int z = 0; z < 4; ++z) sl[z] = u[z] >= 0 ? __ldcg(&R.slot[u[z]]) : 0ull;
+#pragma unroll
+    for (int z = 0; z < 4; ++z)
+      if (u[z] >= 0 && (unsigned)(sl[z] >> 32) == tag) row |= 1u << (sl[z] & 31u);
+  }
+  unsigned longs = __ballot_sync(FULL, mine && !shortrow);
+  while (longs) {
+    const int src = __ffs(longs) - 1;
+    longs &= longs - 1;
+    const int64_t b = __shfl_sync(FULL, rb, src), e = __shfl_sync(FULL, re, src);
+    uint32_t acc = 0u;
+    for (int64_t q = b + l; q < e; q += 32) {
+      const unsigned long long sl = __ldcg(&R.slot[R.adj[q]]);
+      if ((unsigned)(sl >> 32) == tag) acc |= 1u << (sl & 31u);
+    }
+    acc = __reduce_or_sync(FULL, acc);
+    if (l == src) row |= acc;
+  }
+  if (l == 0) {
+    add_ll(&Rg->items, 1ll);
+    add_ll(&Rg->alg_bytes, 20ll * n + 12ll * D);
+  }
+  const uint32_t all = n >= 32 ? 0xffffffffu : (1u << n) - 1u;
+  // 2. input cluster: CCR (Algorithm 1)
+  if (it.flags & ITEM_TOP) {
+    const int k = tiny_components(row, all, cm);
+    if (k != 1) {
+      tiny_emit(P, R, Rg, it, v, cm, k);
+      return true;
+    }
+  }
+  // 3. peel, round-synchronous, T from the alive count
+  uint32_t cur = all;
+  for (;;) {
+    const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, __popc(cur));
+    const unsigned rm = __ballot_sync(FULL, ((cur >> l) & 1u) && __popc(row & cur) <= T);
+    if (!rm) break;
+    cur &= ~rm;
+  }
+  const int nal = __popc(cur);
+  if (nal < n && l == 0) add_ll(&Rg->peeled, (long long)(n - nal));
+  if (nal < R.min_size) return true;
+  // 4. connectivity of what is left (only a peel can disconnect it)
+  if (nal < n) {
+    const int k = tiny_components(row, cur, cm);
+    if (k > 1) {
+      tiny_emit(P, R, Rg, it, v, cm, k);
+      return true;
+    }
+  }
+  // 5-6. contraction with k = T+1, then canonical Stoer-Wagner: the dense
+  // finish on the item's own vertices (index = local id)
+  const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, nal);
+  const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
+  const uint32_t rw = ((cur >> l) & 1u) ? row & cur : 0u;
+#pragma unroll 8
+  for (int b = 0; b < 32; ++b) w[l * 32 + b] = (int32_t)((rw >> b) & 1u);
+  __syncwarp();
+  const DenseResult dr = dense_finish(w, 32, cur, kcap, duf);
+  if (l == 0) {
+    add_ll(&Rg->ni_passes, (long long)dr.passes);
+    add_ll(&Rg->sw_phases, (long long)dr.phases);
+  }
+  if (dr.cut < 0) {
+    // accept (Algorithm 3: save V_c); output id resolved after the run
+    const int32_t minv = __shfl_sync(FULL, v, __ffs(cur) - 1);
+    if ((cur >> l) & 1u) R.label_min[v] = minv;
+    if (l == 0) add_ll(&Rg->accepted, 1ll);
+    return true;
+  }
+  if (dr.cut > T) {
+    if (l == 0) atomicOr(&P.ctr->error, DERR_INTERNAL);
+    return true;
+  }
+  if (l == 0) {
+    add_ll(&Rg->splits, 1ll);
+    cm[0] = cur & ~dr.side;
+    cm[1] = cur & dr.side;
+  }
+  __syncwarp();
+  tiny_emit(P, R, Rg, it, v, cm, 2);
+  return true;
+}
+
+// The end of an item: the request's and the run's pending counts drop (the
+// request's last item raises its host-mapped done flag).  One thread.
+__device__ __forceinline__ void finish_item(const RefineParams &P, uint16_t req) {
+  __threadfence();
+  ReqCtx &R = P.reqs[req];
+  const unsigned long long left =
+      atomicAdd(reinterpret_cast<unsigned long long *>(&R.pending), ~0ull);  // -1
+  if (left == 1ull && P.done_flags) {
+    // the request's last item: everything it wrote is visible first
+    __threadfence_system();
+    ((volatile int *)P.done_flags)[req] = 1;
+  }
+  add_ll(&P.ctr->pending, -1ll);
 }
 
 // ---- one work item ---------------------------------------------------------
@@ -1848,7 +2063,16 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
         }
       }
       __syncthreads();
-      dense_finish(w, nsv, kcap, sh);
+      if (threadIdx.x < 32) {
+        const DenseResult dr = dense_finish(w, nsv, nsv >= 32 ? 0xffffffffu : (1u << nsv) - 1u,
+                                            kcap, sh.duf);
+        if (threadIdx.x == 0) {
+          sh.dcut = dr.cut;
+          sh.dside = dr.side;
+          sh.dpasses = dr.passes;
+          sh.dphases = dr.phases;
+        }
+      }
       __syncthreads();
       passes += sh.dpasses;
       if (threadIdx.x == 0) {
@@ -1996,6 +2220,7 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
   char *slab = P.slab + (size_t)blockIdx.x * P.slab_bytes;
   RunCounters *ctr = P.ctr;
   volatile RunCounters *vctr = ctr;
+  const bool tiny_ok = P.tiny_max > 0 && P.smem_bytes >= (size_t)RW * TINY_SCRATCH;
   for (;;) {
     if (threadIdx.x == 0) {
       int go = 0;
@@ -2055,73 +2280,130 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
         __threadfence();
         if (go) {
           volatile Item *vi = &sl->item;
-          sh.item.vbeg = vi->vbeg;
-          sh.item.n = vi->n;
-          sh.item.flags = vi->flags;
-          sh.item.req = vi->req;
-          sh.seq = j;
+          sh.batch[0].vbeg = vi->vbeg;
+          sh.batch[0].n = vi->n;
+          sh.batch[0].flags = vi->flags;
+          sh.batch[0].req = vi->req;
+          sh.bseq[0] = j;
         }
       }
+      // a tiny input cluster: claim up to RW-1 more at once, one per warp.
+      // A request's input clusters are queued largest first in one range, so
+      // the ones after a tiny one up to the range's end are tiny too; taking
+      // them as a block costs one compare-and-swap and never holds back a
+      // larger item.
+      int nb = go ? 1 : 0;
+      if (go && tiny_ok && !P.single_item && sh.batch[0].n <= P.tiny_max &&
+          (sh.batch[0].flags & ITEM_TOP)) {
+        const unsigned long long send = __ldcg(&P.reqs[sh.batch[0].req].seed_end);
+        for (int tries = 0; nb < RW && tries < 8; ++tries) {
+          if (vctr->error != 0) break;
+          const unsigned long long h = vctr->head, t = vctr->tail;
+          const unsigned long long lim = t < send ? t : send;
+          if (h >= lim) break;
+          const int k = (int)min((unsigned long long)(RW - nb), lim - h);
+          if (atomicCAS(&ctr->head, h, h + k) != h) continue;
+          for (int z = 0; z < k; ++z) {
+            QSlot *sl = &P.ring[(h + z) % P.ring_cap];
+            const uint64_t t1 = globaltimer_ns();
+            unsigned ns2 = 32;
+            bool ok = true;
+            for (;;) {
+              if (*(volatile unsigned long long *)&sl->seq == h + z) break;
+              if (vctr->error != 0 || globaltimer_ns() - t1 > P.wait_limit_ns) {
+                atomicOr(&ctr->error, DERR_TIMEOUT);
+                ok = false;
+                break;
+              }
+              __nanosleep(ns2);
+              ns2 = ns2 < 1024 ? ns2 * 2 : ns2;
+            }
+            if (!ok) break;  // the run is failing; the rest stays unprocessed
+            __threadfence();
+            volatile Item *vi = &sl->item;
+            sh.batch[nb].vbeg = vi->vbeg;
+            sh.batch[nb].n = vi->n;
+            sh.batch[nb].flags = vi->flags;
+            sh.batch[nb].req = vi->req;
+            sh.bseq[nb] = h + z;
+            ++nb;
+          }
+          break;
+        }
+      }
+      sh.nb = nb;
       sh.go = go;
     }
     __syncthreads();
     if (!sh.go) break;
-    const Item it = sh.item;
-    if (P.prof && threadIdx.x == 0) {
-      const long long t = clock64();
-      for (int k = 0; k < 9; ++k) sh.ts[k] = t;
-      sh.used_slab = 0;
-      sh.pf_E = sh.pf_nalive = sh.pf_passes = sh.pf_nsv = -1;
-      sh.pf_forest = sh.pf_nsv1 = 0;
-      sh.pf_forest_cycles = 0;
-      sh.pf_t0 = (long long)globaltimer_ns();
-      for (int k = 0; k < 6; ++k) sh.fdbg[k] = 0;
-      for (int k = 0; k < 4; ++k) sh.dbg[k] = 0;
-    }
+    const int nb = sh.nb;
+    if (threadIdx.x == 0) sh.ntouched = 0;  // bit k: batch item k runs on the CTA
     __syncthreads();
-    const int outcome = run_item(P, sh.seq, it, slab, sh);
-    __syncthreads();
-    if (P.prof && threadIdx.x == 0) {
-      // fill skipped stamps forward, then record
-      sh.ts[8] = clock64();
-      for (int k = 1; k < 8; ++k)
-        if (sh.ts[k] < sh.ts[k - 1]) sh.ts[k] = sh.ts[k - 1];
-      const unsigned r = atomicAdd(P.prof_count, 1u);
-      if (r < P.prof_cap) {
-        ItemProf *q = &P.prof[r];
-        q->seq = (unsigned)sh.seq;
-        q->n = it.n;
-        q->E = sh.pf_E;
-        q->nalive = sh.pf_nalive;
-        q->passes = sh.pf_passes;
-        q->nsv = sh.pf_nsv;
-        q->outcome = outcome;
-        unsigned smid;
-        asm("mov.u32 %0, %%smid;" : "=r"(smid));
-        q->smid = (int)smid;
-        q->slab = sh.used_slab;
-        q->top = (int)(it.flags & ITEM_TOP);
-        for (int k = 0; k < 8; ++k) q->dt[k] = (unsigned)(sh.ts[k + 1] - sh.ts[k]);
-        q->t_begin = sh.pf_t0;
-        q->t_end = (long long)globaltimer_ns();
-        for (int k = 0; k < 4; ++k) q->dbg[k] = sh.dbg[k];
-        q->forest = sh.pf_forest;
-        q->nsv1 = sh.pf_nsv1;
-        q->forest_cycles = sh.pf_forest_cycles;
-        for (int k = 0; k < 6; ++k) q->fdbg[k] = sh.fdbg[k];
+    if (tiny_ok) {
+      const int warp = threadIdx.x >> 5;
+      if (warp < nb && sh.batch[warp].n <= P.tiny_max) {
+        const Item ti = sh.batch[warp];
+        const bool done = tiny_item(P, sh.bseq[warp], ti,
+                                    reinterpret_cast<int32_t *>(wcc_dyn_smem + (size_t)warp * TINY_SCRATCH));
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+          if (done) finish_item(P, ti.req);
+          else atomicOr(&sh.ntouched, 1 << warp);
+        }
       }
+      __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      __threadfence();
-      ReqCtx &R = P.reqs[it.req];
-      const unsigned long long left =
-          atomicAdd(reinterpret_cast<unsigned long long *>(&R.pending), ~0ull);  // -1
-      if (left == 1ull && P.done_flags) {
-        // the request's last item: everything it wrote is visible first
-        __threadfence_system();
-        ((volatile int *)P.done_flags)[it.req] = 1;
+    const int cta_mask = sh.ntouched;
+    for (int k = 0; k < nb; ++k) {
+      const Item it = sh.batch[k];
+      if (tiny_ok && it.n <= P.tiny_max && !((cta_mask >> k) & 1)) continue;
+      const unsigned long long iseq = sh.bseq[k];
+      if (P.prof && threadIdx.x == 0) {
+        const long long t = clock64();
+        for (int z = 0; z < 9; ++z) sh.ts[z] = t;
+        sh.used_slab = 0;
+        sh.pf_E = sh.pf_nalive = sh.pf_passes = sh.pf_nsv = -1;
+        sh.pf_forest = sh.pf_nsv1 = 0;
+        sh.pf_forest_cycles = 0;
+        sh.pf_t0 = (long long)globaltimer_ns();
+        for (int z = 0; z < 6; ++z) sh.fdbg[z] = 0;
+        for (int z = 0; z < 4; ++z) sh.dbg[z] = 0;
       }
-      add_ll(&ctr->pending, -1ll);
+      __syncthreads();
+      const int outcome = run_item(P, iseq, it, slab, sh);
+      __syncthreads();
+      if (P.prof && threadIdx.x == 0) {
+        // fill skipped stamps forward, then record
+        sh.ts[8] = clock64();
+        for (int z = 1; z < 8; ++z)
+          if (sh.ts[z] < sh.ts[z - 1]) sh.ts[z] = sh.ts[z - 1];
+        const unsigned r = atomicAdd(P.prof_count, 1u);
+        if (r < P.prof_cap) {
+          ItemProf *q = &P.prof[r];
+          q->seq = (unsigned)iseq;
+          q->n = it.n;
+          q->E = sh.pf_E;
+          q->nalive = sh.pf_nalive;
+          q->passes = sh.pf_passes;
+          q->nsv = sh.pf_nsv;
+          q->outcome = outcome;
+          unsigned smid;
+          asm("mov.u32 %0, %%smid;" : "=r"(smid));
+          q->smid = (int)smid;
+          q->slab = sh.used_slab;
+          q->top = (int)(it.flags & ITEM_TOP);
+          for (int z = 0; z < 8; ++z) q->dt[z] = (unsigned)(sh.ts[z + 1] - sh.ts[z]);
+          q->t_begin = sh.pf_t0;
+          q->t_end = (long long)globaltimer_ns();
+          for (int z = 0; z < 4; ++z) q->dbg[z] = sh.dbg[z];
+          q->forest = sh.pf_forest;
+          q->nsv1 = sh.pf_nsv1;
+          q->forest_cycles = sh.pf_forest_cycles;
+          for (int z = 0; z < 6; ++z) q->fdbg[z] = sh.fdbg[z];
+        }
+      }
+      if (threadIdx.x == 0) finish_item(P, it.req);
+      __syncthreads();
     }
     if (P.single_item) break;
   }

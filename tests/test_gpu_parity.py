@@ -199,11 +199,13 @@ def _random_workload(seed):
 
 
 # Internal strategy switches (each must leave the result unchanged): the
-# sparse passes only, the forest acceptance test on every item, and working
-# memory in the global slab instead of shared memory.
+# sparse passes only, the forest acceptance test on every item, working
+# memory in the global slab instead of shared memory, and small items on a
+# whole CTA instead of one warp each.
 @pytest.mark.parametrize("env", [{"WCC_DENSE_NSV": "0"}, {"WCC_FOREST_MIN_N": "2"},
-                                 {"WCC_SMEM_KB": "40"},
-                                 {"WCC_DENSE_NSV": "0", "WCC_FOREST_MIN_N": "2", "WCC_SMEM_KB": "40"}])
+                                 {"WCC_SMEM_KB": "40"}, {"WCC_TINY_N": "0"},
+                                 {"WCC_DENSE_NSV": "0", "WCC_FOREST_MIN_N": "2", "WCC_SMEM_KB": "40",
+                                  "WCC_TINY_N": "0"}])
 def test_strategy_switches_keep_results(wcc, monkeypatch, env):
     cases = [synth.planted_1k(0), synth.lfr_like(12000, seed=8)] + [_random_workload(s) for s in range(3)]
     refs = [_oracle(w)[0] for w in cases]
