@@ -213,6 +213,52 @@ void wcc_server_destroy(wcc_server *s);
 int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
                            int64_t *row_off, int32_t *cols, int64_t *nnz, void *stream);
 
+/* ---- tuning ------------------------------------------------------------
+ * The refinement kernel schedules work items by size: items of at most
+ * tiny_max vertices run one per warp (up to 8 per CTA) unless their members'
+ * degree sum exceeds tiny_max_deg; larger items run on a whole CTA in shared
+ * memory (smem_kb per CTA) or, when they do not fit, in a global slab; after
+ * the first contraction pass, at most dense_max super-vertices finish on a
+ * dense weight matrix; items of at least forest_min_n vertices first try the
+ * forest acceptance test.  None of these changes a result, only the time.
+ * The setting is process-wide; the environment variables WCC_TINY_N,
+ * WCC_TINY_DEG, WCC_DENSE_NSV, WCC_FOREST_MIN_N and WCC_SMEM_KB, when set,
+ * take precedence over it. */
+typedef struct wcc_tuning {
+  int32_t tiny_max;      /* 0..32 (0: no item runs on a single warp) */
+  int32_t tiny_max_deg;  /* >= 0 */
+  int32_t dense_max;     /* 0..32 (0: always the sparse passes) */
+  int32_t forest_min_n;  /* >= 0 (0: never) */
+  int32_t smem_kb;       /* >= 0 (0: the largest a CTA can opt into) */
+  int32_t reserved[3];   /* zero */
+} wcc_tuning;
+
+/* Current process-wide tuning (before environment overrides).  Needs no GPU. */
+int wcc_get_tuning(wcc_tuning *out);
+
+/* Sets the process-wide tuning; values outside the ranges above return
+ * WCC_ERR_INVALID and change nothing.  Needs no GPU. */
+int wcc_set_tuning(const wcc_tuning *t);
+
+/* Autotuner: times wcc_run (BATCHED) of this graph and clustering under a
+ * small set of candidate tunings (one knob at a time from the current one,
+ * keeping each improvement), checks that every candidate gives the same
+ * refined clustering (else WCC_ERR_INTERNAL), sets the fastest as the
+ * process-wide tuning and returns it in *best (time of one run in *best_ms,
+ * either may be NULL).  clustering_in as for wcc_run (host or device, per
+ * on_device); stream as for wcc_run.  When cache_path is not NULL the result
+ * is written there as a small JSON object naming the device (see
+ * wcc_load_tuning).  Takes about 2 x (number of candidates) runs. */
+int wcc_autotune(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+                 int32_t min_size, int on_device, void *stream, const char *cache_path,
+                 wcc_tuning *best, double *best_ms);
+
+/* Reads a tuning written by wcc_autotune and sets it process-wide (and
+ * returns it in *out, which may be NULL).  When a GPU is present and the
+ * file names another device model, nothing is set and WCC_ERR_INVALID is
+ * returned; a missing or malformed file also returns WCC_ERR_INVALID. */
+int wcc_load_tuning(const char *cache_path, wcc_tuning *out);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (instrumentation: lets a caller count the kernels of a timed region). */
 int64_t wcc_kernel_launches(void);

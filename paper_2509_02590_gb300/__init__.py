@@ -19,7 +19,8 @@ from ._binding import (WCC_MODE_BATCHED, WCC_MODE_PLAIN, WCC_RULE_LINEAR,  # noq
                        wcc_graph_nnz, wcc_graph_num_vertices, wcc_kernel_launches,
                        wcc_last_error, wcc_poll, wcc_run, wcc_server_create,
                        wcc_server_destroy, wcc_submit, wcc_wait,
-                       wcc_stats, wcc_threshold_rule)
+                       wcc_stats, wcc_threshold_rule, wcc_tuning, wcc_get_tuning,
+                       wcc_set_tuning, wcc_autotune, wcc_load_tuning)
 
 _RULES = {"log10": WCC_RULE_LOG10, "log2": WCC_RULE_LOG2, "sqrt": WCC_RULE_SQRT,
           "linear": WCC_RULE_LINEAR}
@@ -187,9 +188,42 @@ class WccServer:
             pass
 
 
+def get_tuning() -> dict:
+    """The process-wide tuning of the refinement schedule (see include/wcc.h)."""
+    return wcc_get_tuning().as_dict()
+
+
+def set_tuning(**fields) -> dict:
+    """Changes fields of the process-wide tuning; returns the new tuning."""
+    t = wcc_get_tuning()
+    for k, v in fields.items():
+        if k not in t.as_dict():
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    wcc_set_tuning(t)
+    return t.as_dict()
+
+
+def autotune(graph: "WccGraph", labels, min_size: int = 2, rule="log10", num: int = 1,
+             den: int = 1, cache_path: str | None = None):
+    """Times candidate tunings on this graph and clustering, sets the fastest
+    and returns (tuning dict, ms per run)."""
+    pin, dev, stream, _keep = _buf(labels, np.int32)
+    best, ms = wcc_autotune(graph.handle, pin, rule_struct(rule, num, den), min_size, dev, stream,
+                            cache_path)
+    return best.as_dict(), ms
+
+
+def load_tuning(cache_path: str) -> dict:
+    """Sets the tuning that autotune wrote to cache_path; returns it."""
+    return wcc_load_tuning(cache_path).as_dict()
+
+
 __all__ = ["WccServer", "WccGraph", "WccError", "rule_struct", "wcc_create_graph",
            "wcc_create_graph_from_edges", "wcc_run", "wcc_destroy_graph", "wcc_last_error",
            "wcc_graph_num_vertices", "wcc_graph_nnz", "wcc_kernel_launches", "wcc_build_csr_no_alloc", "wcc_graph_export_csr", "wcc_stats",
            "wcc_threshold_rule", "WCC_MODE_BATCHED", "WCC_MODE_PLAIN", "wcc_server_create",
-           "wcc_submit", "wcc_poll", "wcc_wait", "wcc_server_destroy"]
+           "wcc_submit", "wcc_poll", "wcc_wait", "wcc_server_destroy", "wcc_tuning",
+           "wcc_get_tuning", "wcc_set_tuning", "wcc_autotune", "wcc_load_tuning", "get_tuning",
+           "set_tuning", "autotune", "load_tuning"]
 _ = ctypes

@@ -44,6 +44,15 @@ class wcc_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class wcc_tuning(ctypes.Structure):
+    _fields_ = [("tiny_max", ctypes.c_int32), ("tiny_max_deg", ctypes.c_int32),
+                ("dense_max", ctypes.c_int32), ("forest_min_n", ctypes.c_int32),
+                ("smem_kb", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
 class WccError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -91,6 +100,16 @@ def _load():
     L.wcc_kernel_launches.restype = i64
     L.wcc_last_error.argtypes = []
     L.wcc_last_error.restype = ctypes.c_char_p
+    tp = ctypes.POINTER(wcc_tuning)
+    L.wcc_get_tuning.argtypes = [tp]
+    L.wcc_get_tuning.restype = c_int
+    L.wcc_set_tuning.argtypes = [tp]
+    L.wcc_set_tuning.restype = c_int
+    L.wcc_autotune.argtypes = [vp, vp, ctypes.POINTER(wcc_threshold_rule), i32, c_int, vp,
+                               ctypes.c_char_p, tp, ctypes.POINTER(ctypes.c_double)]
+    L.wcc_autotune.restype = c_int
+    L.wcc_load_tuning.argtypes = [ctypes.c_char_p, tp]
+    L.wcc_load_tuning.restype = c_int
     return L
 
 
@@ -188,3 +207,31 @@ def wcc_run(g: int, clustering_in: int, rule: wcc_threshold_rule | None, min_siz
 
 def wcc_destroy_graph(g: int) -> None:
     lib.wcc_destroy_graph(g)
+
+
+def wcc_get_tuning() -> wcc_tuning:
+    t = wcc_tuning()
+    _check(lib.wcc_get_tuning(ctypes.byref(t)))
+    return t
+
+
+def wcc_set_tuning(t: wcc_tuning) -> None:
+    _check(lib.wcc_set_tuning(ctypes.byref(t)))
+
+
+def wcc_autotune(g: int, clustering_in: int, rule: wcc_threshold_rule | None, min_size: int,
+                 on_device: int, stream: int, cache_path: str | None):
+    """(best tuning, ms of one run with it)."""
+    best = wcc_tuning()
+    ms = ctypes.c_double()
+    _check(lib.wcc_autotune(g, clustering_in, ctypes.byref(rule) if rule is not None else None,
+                            min_size, on_device, stream,
+                            cache_path.encode() if cache_path else None, ctypes.byref(best),
+                            ctypes.byref(ms)))
+    return best, ms.value
+
+
+def wcc_load_tuning(cache_path: str) -> wcc_tuning:
+    t = wcc_tuning()
+    _check(lib.wcc_load_tuning(cache_path.encode(), ctypes.byref(t)))
+    return t

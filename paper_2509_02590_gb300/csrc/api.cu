@@ -9,6 +9,8 @@
 #include <memory>
 #include <unordered_map>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace wccg {
@@ -128,9 +130,31 @@ uint64_t wait_limit_ns() {
 // Items of at least this many vertices first try the forest acceptance test
 // (WCC_FOREST_MIN_N; 0, the default, turns it off: on the measured workloads
 // the maximum-adjacency pass decides faster).
+// The process-wide tuning (wcc_set_tuning / wcc_autotune / wcc_load_tuning);
+// an environment variable, when set, overrides its field.
+static std::mutex g_tune_mu;
+static wcc_tuning g_tune = {32, 1024, 32, 0, 0, {0, 0, 0}};
+
+wcc_tuning current_tuning() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune;
+}
+void store_tuning(const wcc_tuning &t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune = t;
+}
+bool tuning_valid(const wcc_tuning &t) {
+  return t.tiny_max >= 0 && t.tiny_max <= 32 && t.tiny_max_deg >= 0 && t.dense_max >= 0 &&
+         t.dense_max <= 32 && t.forest_min_n >= 0 && t.smem_kb >= 0 && t.reserved[0] == 0 &&
+         t.reserved[1] == 0 && t.reserved[2] == 0;
+}
+static long long env_or(const char *name, long long fallback) {
+  const char *e = getenv(name);
+  return e ? atoll(e) : fallback;
+}
+
 int forest_min_n_config() {
-  const char *e = getenv("WCC_FOREST_MIN_N");
-  long long v = e ? atoll(e) : 0;
+  long long v = env_or("WCC_FOREST_MIN_N", current_tuning().forest_min_n);
   if (v < 0) v = 0;
   if (v > (1ll << 30)) v = 1ll << 30;
   return (int)v;
@@ -140,25 +164,30 @@ int forest_min_n_config() {
 // finish takes (WCC_DENSE_NSV, at most 32; 0 keeps every item on the sparse
 // passes).
 int dense_max_config() {
-  const char *e = getenv("WCC_DENSE_NSV");
-  long long v = e ? atoll(e) : 32;
+  const long long v = env_or("WCC_DENSE_NSV", current_tuning().dense_max);
   return (int)(v < 0 ? 0 : v > 32 ? 32 : v);
 }
 
 // Items of at most this many vertices (WCC_TINY_N, at most 32; 0 keeps every
 // item on a whole CTA) are refined one per warp, up to 8 at once per CTA.
 int tiny_max_config() {
-  const char *e = getenv("WCC_TINY_N");
-  long long v = e ? atoll(e) : 32;
+  const long long v = env_or("WCC_TINY_N", current_tuning().tiny_max);
   return (int)(v < 0 ? 0 : v > 32 ? 32 : v);
+}
+
+// ... unless their members' degree sum exceeds WCC_TINY_DEG (a hub's row would
+// keep one warp busy while its CTA waits).
+int tiny_max_deg_config() {
+  const long long v = env_or("WCC_TINY_DEG", current_tuning().tiny_max_deg);
+  return (int)(v < 0 ? 0 : v > (1ll << 30) ? (1ll << 30) : v);
 }
 
 // Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
 // largest a CTA can opt into, one CTA per SM).  Items whose working set is
 // larger use a global slab.
 size_t refine_smem_bytes_config(int device) {
-  const char *e = getenv("WCC_SMEM_KB");
-  long long kb = e ? atoll(e) : (1ll << 30);
+  const int tk = current_tuning().smem_kb;
+  long long kb = env_or("WCC_SMEM_KB", tk > 0 ? tk : (1ll << 30));
   long long mx = (long long)(refine_smem_max_bytes(device) / 1024);
   if (kb < 16) kb = 16;
   if (kb > mx) kb = mx;
@@ -402,6 +431,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     p.forest_min_n = forest_min_n_config();
     p.dense_max = dense_max_config();
     p.tiny_max = tiny_max_config();
+    p.tiny_max_deg = tiny_max_deg_config();
     // optional per-item profile (WCC_PROFILE_ITEMS=<csv path>)
     const char *prof_path = getenv("WCC_PROFILE_ITEMS");
     DevBuf prof_buf;
@@ -645,6 +675,132 @@ void build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64
   *nnz_out = nnz;
 }
 
+// ---- autotuner ---------------------------------------------------------------
+// Coordinate search from the current tuning: each knob in turn tries its
+// other candidate values with the rest fixed, and an improvement of more
+// than 2% is kept.  Every candidate's result must equal the first (the knobs
+// change only the schedule).  A run is timed as the best of two after one
+// warm-up, through the host-buffer path.
+void autotune_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule,
+                   int32_t min_size, int on_device, cudaStream_t s, const char *cache_path,
+                   wcc_tuning *best_out, double *best_ms) {
+  const int64_t n = g->n;
+  if (n > 0 && lab_in == nullptr) fail(WCC_ERR_INVALID, "clustering_in is NULL");
+  std::vector<int32_t> lab((size_t)n), ref((size_t)n), out((size_t)n);
+  if (n > 0) {
+    WCC_CUDA(cudaMemcpyAsync(lab.data(), lab_in, 4 * (size_t)n,
+                             on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    WCC_CUDA(cudaStreamSynchronize(s));
+  }
+  const wcc_tuning start = current_tuning();
+  auto measure = [&](const wcc_tuning &t, std::vector<int32_t> &o) {
+    store_tuning(t);
+    wcc_stats st{};
+    run_impl(g, lab.data(), rule, min_size, WCC_MODE_BATCHED, o.data(), 0, s, &st);
+    double best = 1e300;
+    for (int r = 0; r < 2; ++r) {
+      run_impl(g, lab.data(), rule, min_size, WCC_MODE_BATCHED, o.data(), 0, s, &st);
+      best = std::min(best, st.ms_total);
+    }
+    return best;
+  };
+  wcc_tuning cur = start;
+  double cur_ms = 0.0;
+  try {
+    cur_ms = measure(cur, ref);
+    struct Knob {
+      int32_t wcc_tuning::*field;
+      std::vector<int32_t> values;
+    };
+    const Knob knobs[] = {{&wcc_tuning::tiny_max, {0, 16, 32}},
+                          {&wcc_tuning::tiny_max_deg, {256, 1024, 4096}},
+                          {&wcc_tuning::dense_max, {16, 32}},
+                          {&wcc_tuning::smem_kb, {0, 160}},
+                          {&wcc_tuning::forest_min_n, {0, 48}}};
+    for (const Knob &k : knobs) {
+      const int32_t base = cur.*k.field;
+      for (int32_t v : k.values) {
+        if (v == base) continue;
+        wcc_tuning t = cur;
+        t.*k.field = v;
+        const double ms = measure(t, out);
+        if (out != ref) fail(WCC_ERR_INTERNAL, "a candidate tuning changed the refined clustering");
+        if (ms < 0.98 * cur_ms) {
+          cur = t;
+          cur_ms = ms;
+        }
+      }
+    }
+  } catch (...) {
+    store_tuning(start);
+    throw;
+  }
+  store_tuning(cur);
+  if (cache_path) {
+    cudaDeviceProp prop{};
+    WCC_CUDA(cudaGetDeviceProperties(&prop, g->device));
+    FILE *f = fopen(cache_path, "w");
+    if (!f) fail(WCC_ERR_INVALID, std::string("cannot write ") + cache_path);
+    fprintf(f,
+            "{\"device\": \"%s\", \"sms\": %d, \"n\": %lld, \"nnz\": %lld, \"ms\": %.4f, "
+            "\"tiny_max\": %d, \"tiny_max_deg\": %d, \"dense_max\": %d, \"forest_min_n\": %d, "
+            "\"smem_kb\": %d}\n",
+            prop.name, prop.multiProcessorCount, (long long)g->n, (long long)g->nnz, cur_ms,
+            cur.tiny_max, cur.tiny_max_deg, cur.dense_max, cur.forest_min_n, cur.smem_kb);
+    fclose(f);
+  }
+  if (best_out) *best_out = cur;
+  if (best_ms) *best_ms = cur_ms;
+}
+
+// The value of "key" in the small JSON object written above.
+bool json_int(const std::string &js, const char *key, long long *v) {
+  const std::string k = std::string("\"") + key + "\":";
+  const size_t p = js.find(k);
+  if (p == std::string::npos) return false;
+  char *end = nullptr;
+  *v = strtoll(js.c_str() + p + k.size(), &end, 10);
+  return end != js.c_str() + p + k.size();
+}
+
+void load_tuning_impl(const char *path, wcc_tuning *out) {
+  if (!path) fail(WCC_ERR_INVALID, "cache_path is NULL");
+  FILE *f = fopen(path, "r");
+  if (!f) fail(WCC_ERR_INVALID, std::string("cannot read ") + path);
+  std::string js;
+  char buf[512];
+  size_t r;
+  while ((r = fread(buf, 1, sizeof(buf), f)) > 0 && js.size() < 65536) js.append(buf, r);
+  fclose(f);
+  wcc_tuning t{};
+  long long v;
+  int32_t wcc_tuning::*fields[] = {&wcc_tuning::tiny_max, &wcc_tuning::tiny_max_deg,
+                                   &wcc_tuning::dense_max, &wcc_tuning::forest_min_n,
+                                   &wcc_tuning::smem_kb};
+  const char *names[] = {"tiny_max", "tiny_max_deg", "dense_max", "forest_min_n", "smem_kb"};
+  for (int i = 0; i < 5; ++i) {
+    if (!json_int(js, names[i], &v) || v < INT32_MIN || v > INT32_MAX)
+      fail(WCC_ERR_INVALID, std::string(path) + ": missing or malformed \"" + names[i] + "\"");
+    t.*fields[i] = (int32_t)v;
+  }
+  if (!tuning_valid(t)) fail(WCC_ERR_INVALID, std::string(path) + ": tuning out of range");
+  // the device it was tuned on, when a GPU is there to compare with
+  int count = 0;
+  if (cudaGetDeviceCount(&count) == cudaSuccess && count > 0) {
+    cudaDeviceProp prop{};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+      const std::string want = std::string("\"device\": \"") + prop.name + "\"";
+      if (js.find(want) == std::string::npos)
+        fail(WCC_ERR_INVALID, std::string(path) + " was tuned on another device model");
+    }
+  } else {
+    cudaGetLastError();  // no GPU: nothing to compare with
+  }
+  store_tuning(t);
+  if (out) *out = t;
+}
+
 template <typename F>
 int guarded(F &&f) {
   try {
@@ -744,5 +900,40 @@ int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, in
 int64_t wcc_kernel_launches(void) { return launches_so_far(); }
 
 const char *wcc_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+extern "C" {
+
+int wcc_get_tuning(wcc_tuning *out) {
+  return wccg::guarded([&] {
+    if (!out) wccg::fail(WCC_ERR_INVALID, "out is NULL");
+    *out = wccg::current_tuning();
+  });
+}
+
+int wcc_set_tuning(const wcc_tuning *t) {
+  return wccg::guarded([&] {
+    if (!t) wccg::fail(WCC_ERR_INVALID, "tuning is NULL");
+    if (!wccg::tuning_valid(*t)) wccg::fail(WCC_ERR_INVALID, "tuning out of range");
+    wccg::store_tuning(*t);
+  });
+}
+
+int wcc_autotune(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+                 int32_t min_size, int on_device, void *stream, const char *cache_path,
+                 wcc_tuning *best, double *best_ms) {
+  return wccg::guarded([&] {
+    if (!g || !g->g) wccg::fail(WCC_ERR_INVALID, "graph is NULL");
+    std::lock_guard<std::mutex> lk(g->g->run_mutex);
+    wccg::DeviceGuard dg(g->g->device);
+    wccg::autotune_impl(g->g, clustering_in, rule, min_size, on_device, (cudaStream_t)stream,
+                        cache_path, best, best_ms);
+  });
+}
+
+int wcc_load_tuning(const char *cache_path, wcc_tuning *out) {
+  return wccg::guarded([&] { wccg::load_tuning_impl(cache_path, out); });
+}
 
 }  // extern "C"

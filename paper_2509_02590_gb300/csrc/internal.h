@@ -147,6 +147,7 @@ struct RefineParams {
   int forest_min_n;           // smallest item that tries the forest acceptance test (0 = never)
   int dense_max;              // most super-vertices the dense finish takes (0 = never)
   int tiny_max;               // items of at most this many vertices run one per warp (0 = never)
+  int tiny_max_deg;           // ... when their members' degree sum is at most this
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
   ItemProf *prof;             // optional per-item profile (NULL = off)
@@ -205,6 +206,12 @@ size_t refine_smem_bytes_config(int device);  // WCC_SMEM_KB (default: opt-in ma
 int forest_min_n_config();                    // WCC_FOREST_MIN_N
 int dense_max_config();                       // WCC_DENSE_NSV
 int tiny_max_config();                        // WCC_TINY_N
+int tiny_max_deg_config();                    // WCC_TINY_DEG
+// The process-wide tuning the *_config() functions fall back to.
+wcc_tuning current_tuning();
+void store_tuning(const wcc_tuning &t);
+bool tuning_valid(const wcc_tuning &t);
+
 wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule);
 
 template <typename T>

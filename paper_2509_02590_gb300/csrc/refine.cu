@@ -1654,10 +1654,8 @@ __device__ __forceinline__ int tiny_components(uint32_t row, uint32_t set, uint3
   return k;
 }
 
-constexpr int TINY_MAX_DEG = 1024;  // larger degree sums go to the whole CTA
-
 // Returns false, having done nothing, when the members' degree sum exceeds
-// TINY_MAX_DEG (a hub's row would keep one warp busy while its CTA waits).
+// P.tiny_max_deg (a hub's row would keep one warp busy while its CTA waits).
 __device__ bool tiny_item(const RefineParams &P, unsigned long long seq, const Item &it,
                           int32_t *scratch) {
   const int l = threadIdx.x & 31;
@@ -1672,7 +1670,7 @@ __device__ bool tiny_item(const RefineParams &P, unsigned long long seq, const I
   const uint32_t tag = queue_tag(seq);
   const int len = (int)(re - rb);
   const long long D = warp_sum((long long)(mine ? len : 0));
-  if (D > TINY_MAX_DEG) return false;
+  if (D > P.tiny_max_deg) return false;
   // 1. extraction: rows of up to 64 entries by their own lane, four entries
   // at a time; longer rows by the whole warp, one after the other
   const bool shortrow = len <= 64;

@@ -225,6 +225,7 @@ void launch_kernel(Server *S) {
   p.forest_min_n = forest_min_n_config();
   p.dense_max = dense_max_config();
   p.tiny_max = tiny_max_config();
+  p.tiny_max_deg = tiny_max_deg_config();
   p.slab = S->slab.as<char>();
   p.slab_bytes = S->slab_bytes;
   // a previous instance may have closed on idling out; the launch reopens
