@@ -259,6 +259,35 @@ int wcc_autotune(const wcc_graph *g, const int32_t *clustering_in, const wcc_thr
  * returned; a missing or malformed file also returns WCC_ERR_INVALID. */
 int wcc_load_tuning(const char *cache_path, wcc_tuning *out);
 
+/* ---- resumable runs (checkpoint / resume) ----------------------------------
+ * A job is wcc_run in steps.  wcc_job_start groups the clustering and queues
+ * the input clusters (Algorithm 1's loop) without refining anything;
+ * wcc_job_step runs the refinement until the queue is empty (WCC_OK) or
+ * time_budget_ms has passed (WCC_PENDING: the kernel stopped at an item
+ * boundary, every queued item is kept; time_budget_ms < 0: no limit).
+ * Every CTA of a step takes one queued item before it looks at the time, so
+ * each step that returns WCC_PENDING has made progress, even with budget 0.
+ * wcc_job_save writes the queue -- the queued items' vertex lists, the
+ * clusters accepted so far, the statistics -- to a file; wcc_job_load
+ * rebuilds a job from it on a graph with the same vertex and edge counts
+ * (the graph itself is not stored: load it onto the same graph).
+ * wcc_job_finish, once a step has returned WCC_OK (else WCC_ERR_BUSY),
+ * writes the refined clustering exactly as wcc_run would, with the same
+ * conventions for clustering_out / on_device / stream / stats.  The result
+ * does not depend on where the steps stopped or on a save/load in between.
+ * A job uses its graph until wcc_job_destroy; destroy jobs before their
+ * graph.  Loading checks a checksum and returns WCC_ERR_INVALID on a
+ * corrupt, truncated or foreign file. */
+typedef struct wcc_job wcc_job;
+int wcc_job_start(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+                  int32_t min_size, int on_device, void *stream, wcc_job **out);
+int wcc_job_step(wcc_job *job, int64_t time_budget_ms, void *stream);
+int wcc_job_save(wcc_job *job, const char *path, void *stream);
+int wcc_job_load(const wcc_graph *g, const char *path, void *stream, wcc_job **out);
+int wcc_job_finish(wcc_job *job, int32_t *clustering_out, int on_device, void *stream,
+                   wcc_stats *stats);
+void wcc_job_destroy(wcc_job *job);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (instrumentation: lets a caller count the kernels of a timed region). */
 int64_t wcc_kernel_launches(void);

@@ -20,7 +20,9 @@ from ._binding import (WCC_MODE_BATCHED, WCC_MODE_PLAIN, WCC_RULE_LINEAR,  # noq
                        wcc_last_error, wcc_poll, wcc_run, wcc_server_create,
                        wcc_server_destroy, wcc_submit, wcc_wait,
                        wcc_stats, wcc_threshold_rule, wcc_tuning, wcc_get_tuning,
-                       wcc_set_tuning, wcc_autotune, wcc_load_tuning)
+                       wcc_set_tuning, wcc_autotune, wcc_load_tuning, wcc_job_start,
+                       wcc_job_step, wcc_job_save, wcc_job_load, wcc_job_finish,
+                       wcc_job_destroy)
 
 _RULES = {"log10": WCC_RULE_LOG10, "log2": WCC_RULE_LOG2, "sqrt": WCC_RULE_SQRT,
           "linear": WCC_RULE_LINEAR}
@@ -188,6 +190,61 @@ class WccServer:
             pass
 
 
+class WccJob:
+    """A refinement in resumable steps (owns a ``wcc_job``): ``step`` runs for
+    a time budget, ``save`` / ``WccJob.load`` checkpoint the queue to a file,
+    ``finish`` gives the refined clustering once ``step`` has returned True.
+    Host (numpy) clusterings; the graph must stay open while the job lives."""
+
+    def __init__(self, handle: int, graph: WccGraph):
+        self.handle = handle
+        self.graph = graph
+
+    @classmethod
+    def start(cls, graph: WccGraph, labels, min_size: int = 2, rule="log10", num: int = 1,
+              den: int = 1) -> "WccJob":
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        if len(lab) != graph.n:
+            raise ValueError("labels must have one entry per vertex")
+        return cls(wcc_job_start(graph.handle, lab.ctypes.data, rule_struct(rule, num, den),
+                                 min_size, 0, 0), graph)
+
+    @classmethod
+    def load(cls, graph: WccGraph, path: str) -> "WccJob":
+        return cls(wcc_job_load(graph.handle, str(path), 0), graph)
+
+    def step(self, time_budget_ms: int = -1) -> bool:
+        """True once the queue is empty."""
+        return wcc_job_step(self.handle, int(time_budget_ms), 0) == _binding.WCC_OK
+
+    def save(self, path: str) -> None:
+        wcc_job_save(self.handle, str(path), 0)
+
+    def finish(self, stats: bool = False):
+        out = np.empty(max(self.graph.n, 1), np.int32)
+        st = wcc_stats() if stats else None
+        wcc_job_finish(self.handle, out.ctypes.data, 0, 0, st)
+        out = out[:self.graph.n]
+        return (out, st.as_dict()) if stats else out
+
+    def close(self):
+        if self.handle:
+            wcc_job_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def get_tuning() -> dict:
     """The process-wide tuning of the refinement schedule (see include/wcc.h)."""
     return wcc_get_tuning().as_dict()
@@ -225,5 +282,6 @@ __all__ = ["WccServer", "WccGraph", "WccError", "rule_struct", "wcc_create_graph
            "wcc_threshold_rule", "WCC_MODE_BATCHED", "WCC_MODE_PLAIN", "wcc_server_create",
            "wcc_submit", "wcc_poll", "wcc_wait", "wcc_server_destroy", "wcc_tuning",
            "wcc_get_tuning", "wcc_set_tuning", "wcc_autotune", "wcc_load_tuning", "get_tuning",
-           "set_tuning", "autotune", "load_tuning"]
+           "set_tuning", "autotune", "load_tuning", "WccJob", "wcc_job_start", "wcc_job_step",
+           "wcc_job_save", "wcc_job_load", "wcc_job_finish", "wcc_job_destroy"]
 _ = ctypes

@@ -110,6 +110,19 @@ def _load():
     L.wcc_autotune.restype = c_int
     L.wcc_load_tuning.argtypes = [ctypes.c_char_p, tp]
     L.wcc_load_tuning.restype = c_int
+    L.wcc_job_start.argtypes = [vp, vp, ctypes.POINTER(wcc_threshold_rule), i32, c_int, vp,
+                                ctypes.POINTER(vp)]
+    L.wcc_job_start.restype = c_int
+    L.wcc_job_step.argtypes = [vp, i64, vp]
+    L.wcc_job_step.restype = c_int
+    L.wcc_job_save.argtypes = [vp, ctypes.c_char_p, vp]
+    L.wcc_job_save.restype = c_int
+    L.wcc_job_load.argtypes = [vp, ctypes.c_char_p, vp, ctypes.POINTER(vp)]
+    L.wcc_job_load.restype = c_int
+    L.wcc_job_finish.argtypes = [vp, vp, c_int, vp, ctypes.POINTER(wcc_stats)]
+    L.wcc_job_finish.restype = c_int
+    L.wcc_job_destroy.argtypes = [vp]
+    L.wcc_job_destroy.restype = None
     return L
 
 
@@ -235,3 +248,36 @@ def wcc_load_tuning(cache_path: str) -> wcc_tuning:
     t = wcc_tuning()
     _check(lib.wcc_load_tuning(cache_path.encode(), ctypes.byref(t)))
     return t
+
+
+def wcc_job_start(g: int, clustering_in: int, rule: wcc_threshold_rule | None, min_size: int,
+                  on_device: int, stream: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.wcc_job_start(g, clustering_in, ctypes.byref(rule) if rule is not None else None,
+                             min_size, on_device, stream, ctypes.byref(out)))
+    return out.value
+
+
+def wcc_job_step(job: int, time_budget_ms: int, stream: int) -> int:
+    """WCC_OK (queue drained) or WCC_PENDING (time up, work left)."""
+    return _check(lib.wcc_job_step(job, time_budget_ms, stream))
+
+
+def wcc_job_save(job: int, path: str, stream: int) -> None:
+    _check(lib.wcc_job_save(job, path.encode(), stream))
+
+
+def wcc_job_load(g: int, path: str, stream: int) -> int:
+    out = ctypes.c_void_p()
+    _check(lib.wcc_job_load(g, path.encode(), stream, ctypes.byref(out)))
+    return out.value
+
+
+def wcc_job_finish(job: int, clustering_out: int, on_device: int, stream: int,
+                   stats: wcc_stats | None) -> None:
+    _check(lib.wcc_job_finish(job, clustering_out, on_device, stream,
+                              ctypes.byref(stats) if stats is not None else None))
+
+
+def wcc_job_destroy(job: int) -> None:
+    lib.wcc_job_destroy(job)

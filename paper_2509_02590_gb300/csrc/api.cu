@@ -937,3 +937,70 @@ int wcc_load_tuning(const char *cache_path, wcc_tuning *out) {
 }
 
 }  // extern "C"
+
+struct wcc_job {
+  wccg::Job *j;
+  const wcc_graph *g;
+};
+
+extern "C" {
+
+int wcc_job_start(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+                  int32_t min_size, int on_device, void *stream, wcc_job **out) {
+  return wccg::guarded([&] {
+    if (!g || !g->g || !out) wccg::fail(WCC_ERR_INVALID, "graph and out must not be NULL");
+    std::lock_guard<std::mutex> lk(g->g->run_mutex);
+    wccg::DeviceGuard dg(g->g->device);
+    wccg::Job *j = wccg::job_start(g->g, clustering_in, rule, min_size, on_device,
+                                   (cudaStream_t)stream);
+    *out = new wcc_job{j, g};
+  });
+}
+
+int wcc_job_step(wcc_job *job, int64_t time_budget_ms, void *stream) {
+  int st = WCC_OK;
+  const int r = wccg::guarded([&] {
+    if (!job) wccg::fail(WCC_ERR_INVALID, "job is NULL");
+    wccg::DeviceGuard dg(job->g->g->device);
+    st = wccg::job_step(job->j, time_budget_ms, (cudaStream_t)stream) ? WCC_OK : WCC_PENDING;
+  });
+  return r == WCC_OK ? st : r;
+}
+
+int wcc_job_save(wcc_job *job, const char *path, void *stream) {
+  return wccg::guarded([&] {
+    if (!job) wccg::fail(WCC_ERR_INVALID, "job is NULL");
+    wccg::DeviceGuard dg(job->g->g->device);
+    wccg::job_save(job->j, path, (cudaStream_t)stream);
+  });
+}
+
+int wcc_job_load(const wcc_graph *g, const char *path, void *stream, wcc_job **out) {
+  return wccg::guarded([&] {
+    if (!g || !g->g || !out) wccg::fail(WCC_ERR_INVALID, "graph and out must not be NULL");
+    wccg::DeviceGuard dg(g->g->device);
+    wccg::Job *j = wccg::job_load(g->g, path, (cudaStream_t)stream);
+    *out = new wcc_job{j, g};
+  });
+}
+
+int wcc_job_finish(wcc_job *job, int32_t *clustering_out, int on_device, void *stream,
+                   wcc_stats *stats) {
+  return wccg::guarded([&] {
+    if (!job) wccg::fail(WCC_ERR_INVALID, "job is NULL");
+    std::lock_guard<std::mutex> lk(job->g->g->run_mutex);
+    wccg::DeviceGuard dg(job->g->g->device);
+    wccg::job_finish(job->j, clustering_out, on_device, (cudaStream_t)stream, stats);
+  });
+}
+
+void wcc_job_destroy(wcc_job *job) {
+  if (!job) return;
+  wccg::guarded([&] {
+    wccg::DeviceGuard dg(job->g->g->device);
+    wccg::job_destroy(job->j);
+  });
+  delete job;
+}
+
+}  // extern "C"

@@ -148,6 +148,7 @@ struct RefineParams {
   int dense_max;              // most super-vertices the dense finish takes (0 = never)
   int tiny_max;               // items of at most this many vertices run one per warp (0 = never)
   int tiny_max_deg;           // ... when their members' degree sum is at most this
+  const volatile int *stop_flag;  // optional, host-mapped: when nonzero, CTAs claim nothing more
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
   ItemProf *prof;             // optional per-item profile (NULL = off)
@@ -207,6 +208,16 @@ int forest_min_n_config();                    // WCC_FOREST_MIN_N
 int dense_max_config();                       // WCC_DENSE_NSV
 int tiny_max_config();                        // WCC_TINY_N
 int tiny_max_deg_config();                    // WCC_TINY_DEG
+
+// ---- job.cu: a refinement in resumable steps --------------------------------
+struct Job;
+Job *job_start(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, int32_t min_size,
+               int on_device, cudaStream_t s);
+bool job_step(Job *j, int64_t budget_ms, cudaStream_t s);  // true: the queue is empty
+void job_finish(Job *j, int32_t *out, int on_device, cudaStream_t s, wcc_stats *stats);
+void job_save(Job *j, const char *path, cudaStream_t s);
+Job *job_load(Graph *g, const char *path, cudaStream_t s);
+void job_destroy(Job *j);
 // The process-wide tuning the *_config() functions fall back to.
 wcc_tuning current_tuning();
 void store_tuning(const wcc_tuning &t);

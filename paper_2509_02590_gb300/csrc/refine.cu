@@ -2219,6 +2219,7 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
   RunCounters *ctr = P.ctr;
   volatile RunCounters *vctr = ctr;
   const bool tiny_ok = P.tiny_max > 0 && P.smem_bytes >= (size_t)RW * TINY_SCRATCH;
+  bool took = false;  // thread 0: this CTA has claimed an item in this launch
   for (;;) {
     if (threadIdx.x == 0) {
       int go = 0;
@@ -2232,15 +2233,21 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
           go = 1;
           break;
         }
+        // a job step whose time is up: leave at this item boundary (the
+        // queue keeps everything not yet claimed).  A CTA takes one item
+        // before it looks, so that every step makes progress.
+        if (P.stop_flag && took && *P.stop_flag) break;
         const unsigned long long h = vctr->head, t = vctr->tail;
         if (h < t) {
           if (atomicCAS(&ctr->head, h, h + 1) == h) {
             j = h;
             go = 1;
+            took = true;
             break;
           }
           continue;
         }
+        if (P.stop_flag && *P.stop_flag) break;
         // an open (serving) kernel leaves as a whole: the first CTA that
         // idled out closes it for all, so that work admitted meanwhile never
         // runs on a few stragglers; the host relaunches it for that work
@@ -2292,7 +2299,7 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
       // larger item.
       int nb = go ? 1 : 0;
       if (go && tiny_ok && !P.single_item && sh.batch[0].n <= P.tiny_max &&
-          (sh.batch[0].flags & ITEM_TOP)) {
+          (sh.batch[0].flags & ITEM_TOP) && !(P.stop_flag && *P.stop_flag)) {
         const unsigned long long send = __ldcg(&P.reqs[sh.batch[0].req].seed_end);
         for (int tries = 0; nb < RW && tries < 8; ++tries) {
           if (vctr->error != 0) break;
