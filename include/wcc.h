@@ -88,7 +88,8 @@ typedef struct {
   int64_t ni_passes;     /* contraction passes (maximum-adjacency orderings) */
   int64_t sw_phases;     /* Stoer-Wagner phases */
   int64_t max_item;      /* largest input cluster refined (vertices) */
-  int64_t alg_bytes;     /* algorithmic HBM bytes of the run */
+  int64_t alg_bytes;     /* algorithmic HBM bytes of the run: 20 B per item member (id, row
+                          * bounds) plus 12 B per adjacency entry read (id, slot tag) */
   double ms_membership;  /* device time: grouping vertices by input label */
   double ms_refine;      /* device time: the refinement kernel(s) */
   double ms_output;      /* device time: numbering the accepted clusters */
