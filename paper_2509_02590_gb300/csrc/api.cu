@@ -352,7 +352,7 @@ struct Timer {
 };
 
 
-enum RunBuf { R_IN, R_OUT, R_POOL, R_SLOT, R_LMIN, R_RING, R_CTR, R_SLAB, R_REQ, R_COUNT };
+enum RunBuf { R_IN, R_OUT, R_POOL, R_SLOT, R_LMIN, R_RING, R_CTR, R_SLAB, R_REQ, R_INH, R_COUNT };
 static_assert(R_COUNT <= 16, "run buffers");
 
 void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, int32_t min_size,
@@ -391,6 +391,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
   int32_t *pool = static_cast<int32_t *>(rb[R_POOL].ensure(4 * std::max<int64_t>(n - gi.skip, 1)));
   auto *slot = static_cast<unsigned long long *>(rb[R_SLOT].ensure(8 * n));
   auto *lmin = static_cast<int32_t *>(rb[R_LMIN].ensure(4 * n));
+  auto *inh = static_cast<unsigned long long *>(rb[R_INH].ensure(8 * n));
   auto *ring = static_cast<QSlot *>(rb[R_RING].ensure(sizeof(QSlot) * cap));
   auto *ctr = static_cast<RunCounters *>(rb[R_CTR].ensure(sizeof(RunCounters)));
   auto *req = static_cast<ReqCtx *>(rb[R_REQ].ensure(sizeof(ReqCtx)));
@@ -404,6 +405,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
   hreq.pool = pool;
   hreq.slot = slot;
   hreq.label_min = lmin;
+  hreq.inh = inh;
   hreq.rule_kind = r.kind;
   hreq.min_size = min_size;
   hreq.rule_num = r.num;

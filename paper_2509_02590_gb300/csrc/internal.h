@@ -78,10 +78,11 @@ struct Graph {
 struct Item {
   int64_t vbeg;   // start of the item's vertex list in its request's vertex pool
   int32_t n;      // vertices
-  uint16_t flags; // ITEM_TOP: an input cluster (CCR first, Algorithm 1)
+  uint16_t flags; // ITEM_TOP: an input cluster (CCR first, Algorithm 1);
+                  // ITEM_INH: a side of a cut split whose parent left first-pass records
   uint16_t req;   // request it belongs to (index into the request table)
 };
-enum : uint16_t { ITEM_TOP = 1u };
+enum : uint16_t { ITEM_TOP = 1u, ITEM_INH = 2u };
 
 // One refinement request: its graph, its per-vertex state and its counters.
 // wcc_run uses one; a server keeps a table of them for the requests it has
@@ -93,6 +94,8 @@ struct ReqCtx {
   int32_t *pool;               // vertex lists of all the request's items
   unsigned long long *slot;    // per vertex: (queue index << 32) | local id, ~0 = none
   int32_t *label_min;          // per vertex: smallest vertex id of its accepted cluster, or -1
+  unsigned long long *inh;     // per vertex: record of the last first contraction pass over it
+                               // (kcap << 56 | position << 32 | root vertex id); NULL = unused
   int32_t rule_kind, min_size;
   int64_t rule_num, rule_den;
   long long pending;           // published but unfinished items of this request

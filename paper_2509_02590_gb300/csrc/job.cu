@@ -33,7 +33,7 @@ struct Job {
   uint64_t cap = 0;
   int grid = 0;
   size_t smem_bytes = 0, slab_bytes = 0;
-  DevBuf pool, slot, lmin, ring, ctr, req, slab, out;
+  DevBuf pool, slot, lmin, inh, ring, ctr, req, slab, out;
   int *stop_host = nullptr, *stop_dev = nullptr;
   bool done = false;
   ~Job() {
@@ -67,6 +67,7 @@ void sizes_for(Job &j) {
 void alloc_common(Job &j) {
   j.slot.ensure(8 * (size_t)std::max<int64_t>(j.n, 1));
   j.lmin.ensure(4 * (size_t)std::max<int64_t>(j.n, 1));
+  j.inh.ensure(8 * (size_t)std::max<int64_t>(j.n, 1));
   j.ring.ensure(sizeof(QSlot) * j.cap);
   j.ctr.ensure(sizeof(RunCounters));
   j.req.ensure(sizeof(ReqCtx));
@@ -84,6 +85,7 @@ ReqCtx request_of(const Job &j) {
   h.pool = j.pool.as<int32_t>();
   h.slot = j.slot.as<unsigned long long>();
   h.label_min = j.lmin.as<int32_t>();
+  h.inh = j.inh.as<unsigned long long>();
   h.rule_kind = j.rule.kind;
   h.min_size = j.min_size;
   h.rule_num = j.rule.num;
@@ -292,7 +294,8 @@ void job_save(Job *j, const char *path, cudaStream_t s) {
     w.put(M);
     for (uint64_t i = 0; i < P; ++i) {
       w.put((int32_t)q[i].item.n);
-      w.put((int32_t)q[i].item.flags);
+      // first-pass records are not saved: a resumed item computes its own
+      w.put((int32_t)(q[i].item.flags & ITEM_TOP));
     }
     for (uint64_t i = 0; i < P; ++i) w.put(pool.data() + q[i].item.vbeg, 4 * (size_t)q[i].item.n);
     if (j->n) w.put(lmin.data(), 4 * (size_t)j->n);
@@ -368,7 +371,7 @@ Job *job_load(Graph *g, const char *path, cudaStream_t s) {
     for (int64_t i = 0; i < P; ++i) {
       q[i].item.vbeg = at;
       q[i].item.n = sizes[i];
-      q[i].item.flags = (uint16_t)flags[i];
+      q[i].item.flags = (uint16_t)(flags[i] & ITEM_TOP);
       q[i].item.req = 0;
       q[i].seq = (uint64_t)i;
       at += sizes[i];

@@ -49,6 +49,9 @@ extern __shared__ __align__(16) char wcc_dyn_smem[];
 // bitmap word, so "largest key, then smallest id" is the highest non-empty
 // bucket's lowest set bit.  Caps above KB_LEVELS-1 use the linear argmax.
 constexpr int KB_LEVELS = 16;
+// Items whose first contraction pass covers at least this many vertices
+// record it for the sides of a later cut.
+constexpr int INH_MIN_N = 64;
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ inline int bm_words(int64_t n) { return (int)((n + 31) / 32); }
@@ -192,6 +195,8 @@ __device__ __forceinline__ ReqCtx load_ctx(const ReqCtx *g) {
       __ldcg(reinterpret_cast<const unsigned long long *>(&g->slot)));
   r.label_min =
       reinterpret_cast<int32_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&g->label_min)));
+  r.inh = reinterpret_cast<unsigned long long *>(
+      __ldcg(reinterpret_cast<const unsigned long long *>(&g->inh)));
   r.rule_kind = __ldcg(&g->rule_kind);
   r.min_size = __ldcg(&g->min_size);
   r.rule_num = __ldcg(reinterpret_cast<const long long *>(&g->rule_num));
@@ -465,7 +470,8 @@ __device__ __forceinline__ int components_af(const Mem<IT> &m, int n, int32_t *f
 template <typename IT>
 __device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCtx &R,
                                               ReqCtx *Rg, uint16_t req, const Mem<IT> &m,
-                                              const int32_t *tag, int n, int64_t vbeg, Sh &sh) {
+                                              const int32_t *tag, int n, int64_t vbeg, Sh &sh,
+                                              uint16_t cflags = 0) {
   int32_t *cnt = m.C, *cidx = m.D, *cbase = m.E, *run = m.F;
   for (int t = threadIdx.x; t < n; t += RB) cnt[t] = 0;
   __syncthreads();
@@ -521,7 +527,7 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCt
     QSlot *sl = &P.ring[q % P.ring_cap];
     sl->item.vbeg = vbeg + cbase[t];
     sl->item.n = cnt[t];
-    sl->item.flags = 0;
+    sl->item.flags = cflags;
     sl->item.req = req;
   }
   __threadfence();
@@ -1988,6 +1994,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   int nsv = 1, passes = 0;
   int dense_cut = -1;  // >= 0: the dense finish found the cut (side in m.side)
   bool certified = false;
+  bool inh_valid = false;  // R.inh holds this item's first-pass records
   if (kcap <= FOREST_MAX_K && P.forest_min_n > 0 && nalive >= P.forest_min_n) {
     const long long f0 = P.prof ? clock64() : 0;
     const int fr = forest_accept(m, n, kcap, sh, P.prof != nullptr);
@@ -2004,15 +2011,62 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
     if (bucketed) {
       if (threadIdx.x == 0) add_ll(&ctr->ni_passes, 1ll);
       ++passes;
-      const bool any = ma_pass_first(P, m, nrep, n, nalive, kcap, E, &P.ctr->error, sh);
-      int r1 = 0;
-      for (int i = threadIdx.x; i < n; i += RB) {
-        const int r = m.alive[i] ? (any ? nrep[i] : i) : -1;
-        rep[i] = r;
-        r1 += r == i;
+      // A side S of a parent's cut (value <= T) whose members are the first
+      // |S| vertices of the parent's first-pass order, with the same kcap
+      // and nothing peeled here, would run exactly that order's prefix: at
+      // every step of it the parent took the unvisited vertex of largest
+      // capped key, smallest id, and before the order left S no vertex
+      // outside S had been added, so S's keys and saturation steps are the
+      // same in the induced subgraph.  No entry between S and the other
+      // side is contracted (its far end would have kcap > T neighbours in
+      // S, across a cut of at most T), so the parent's first-pass sets on S
+      // are this item's.  Their roots are taken from the records instead of
+      // repeating the pass; any record that does not fit falls back to it.
+      bool inherited = false;
+      if ((it.flags & ITEM_INH) && R.inh != nullptr && nalive == n) {
+        int bad = 0;
+        for (int i = threadIdx.x; i < n; i += RB) {
+          const unsigned long long rec = __ldcg(&R.inh[m.gid[i]]);
+          const int kc = (int)(rec >> 56), p = (int)((rec >> 32) & 0xffffffu);
+          const long long r = (long long)(uint32_t)rec;
+          int loc = -1;
+          if (kc == kcap && p < n && r < R.n_vertices) {
+            const unsigned long long sr = __ldcg(&R.slot[r]);
+            if ((unsigned)(sr >> 32) == queue_tag(seq)) loc = (int)(unsigned)(sr & 0xffffffffu);
+          }
+          if (loc < 0 || loc > i) bad = 1;  // a root is the smallest member of its set
+          rep[i] = loc;
+        }
+        if (!__syncthreads_or(bad)) {
+          for (int i = threadIdx.x; i < n; i += RB)
+            if (rep[rep[i]] != rep[i]) bad = 1;
+          inherited = !__syncthreads_or(bad);
+        }
       }
-      nsv = block_sum_int(r1, sh);
-      more = any;
+      int r1 = 0;
+      if (inherited) {
+        for (int i = threadIdx.x; i < n; i += RB) r1 += rep[i] == i;
+        nsv = block_sum_int(r1, sh);
+        more = nsv < nalive;  // the pass contracted something
+        inh_valid = true;
+      } else {
+        const bool any = ma_pass_first(P, m, nrep, n, nalive, kcap, E, &P.ctr->error, sh);
+        // this pass's records, for the sides of a later cut (position in
+        // m.F, root as a vertex id)
+        const bool rec = R.inh != nullptr && nalive >= INH_MIN_N;
+        const int32_t *pos = m.F;
+        for (int i = threadIdx.x; i < n; i += RB) {
+          const int r = m.alive[i] ? (any ? nrep[i] : i) : -1;
+          rep[i] = r;
+          r1 += r == i;
+          if (rec && r >= 0)
+            R.inh[m.gid[i]] = ((unsigned long long)kcap << 56) |
+                              ((unsigned long long)(unsigned)pos[i] << 32) | (unsigned)m.gid[r];
+        }
+        nsv = block_sum_int(r1, sh);
+        more = any;
+        inh_valid = rec;
+      }
       if (P.prof && threadIdx.x == 0) sh.pf_nsv1 = nsv;
     } else {
       for (int i = threadIdx.x; i < n; i += RB) rep[i] = m.alive[i] ? i : -1;
@@ -2171,7 +2225,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (threadIdx.x == 0) add_ll(&ctr->splits, 1ll);
   for (int i = threadIdx.x; i < n; i += RB) m.B[i] = m.alive[i] ? (m.side[i] ? 1 : 0) : -1;
   __syncthreads();
-  emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh);
+  emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh, inh_valid ? ITEM_INH : (uint16_t)0);
   return OUT_CUT_SPLIT;
 }
 

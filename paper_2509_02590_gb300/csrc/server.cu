@@ -55,7 +55,7 @@ struct Request {
   // device state while admitted
   int slot = -1;
   Workspace ws;
-  DevBuf d_in, d_out, pool, vslot, lmin;
+  DevBuf d_in, d_out, pool, vslot, lmin, inh;
   GroupInfo gi{};
   ~Request() {
     if (h_in) cudaFreeHost(h_in);
@@ -68,14 +68,15 @@ struct Request {
     pool.release();
     vslot.release();
     lmin.release();
+    inh.release();
   }
 };
 
 // Device bytes one request of n vertices may hold at once: its state (input
-// and output labels, vertex pool, slots, cluster minima) and the grouping
-// workspace, about 112 bytes per vertex, doubled for the power-of-two block
-// rounding of the allocator, plus 1 MB.
-size_t estimate_bytes(int64_t n) { return (size_t)n * 224 + (1u << 20); }
+// and output labels, vertex pool, slots, cluster minima, first-pass records)
+// and the grouping workspace, about 120 bytes per vertex, doubled for the
+// power-of-two block rounding of the allocator, plus 1 MB.
+size_t estimate_bytes(int64_t n) { return (size_t)n * 240 + (1u << 20); }
 
 struct Server {
   int device = 0;
@@ -184,6 +185,7 @@ void admit(Server *S, Request *R) {
     int32_t *pool = static_cast<int32_t *>(R->pool.ensure(4 * std::max<int64_t>(n - R->gi.skip, 1)));
     auto *vslot = static_cast<unsigned long long *>(R->vslot.ensure(8 * n));
     auto *lmin = static_cast<int32_t *>(R->lmin.ensure(4 * n));
+    auto *inh = static_cast<unsigned long long *>(R->inh.ensure(8 * n));
     R->d_out.ensure(4 * n);
     WCC_CUDA(cudaMemsetAsync(vslot, 0xff, 8 * n, s));
     WCC_CUDA(cudaMemsetAsync(lmin, 0xff, 4 * n, s));
@@ -194,6 +196,7 @@ void admit(Server *S, Request *R) {
     h.pool = pool;
     h.slot = vslot;
     h.label_min = lmin;
+    h.inh = inh;
     h.rule_kind = R->rule.kind;
     h.min_size = R->min_size;
     h.rule_num = R->rule.num;
