@@ -125,6 +125,45 @@ def test_other_rules(wcc, rule, num, den):
     assert np.array_equal(out, ref)
 
 
+def _block_chains(seed):
+    """Input clusters that are chains of dense blocks joined by one or two
+    edges: every split cuts one link, and the side holding the smallest id
+    is usually a prefix of the parent's first contraction pass, so its own
+    sides inherit again, several levels deep.  Ids are either in block order
+    or shuffled within each cluster."""
+    rng = np.random.default_rng(seed)
+    src, dst, lab = [], [], []
+    n = 0
+    for c in range(int(rng.integers(6, 12))):
+        nb = int(rng.integers(1, 8))
+        sizes = rng.integers(40, 400, size=nb)
+        tot = int(sizes.sum())
+        perm = rng.permutation(tot) if rng.random() < 0.5 else np.arange(tot)
+        starts = np.concatenate([[0], np.cumsum(sizes)])
+        for b in range(nb):
+            a, d = synth.random_gnp(int(sizes[b]), float(rng.uniform(0.06, 0.3)), rng)
+            src.append(n + perm[starts[b] + a]); dst.append(n + perm[starts[b] + d])
+            if b + 1 < nb:
+                k = int(rng.integers(1, 3))
+                src.append(n + perm[starts[b] + rng.integers(0, sizes[b], k)])
+                dst.append(n + perm[starts[b + 1] + rng.integers(0, sizes[b + 1], k)])
+        lab.append(np.full(tot, c, np.int32))
+        n += tot
+    s, d = synth.graphs._dedup(n, np.concatenate(src), np.concatenate(dst))
+    return synth.Workload("chains", n, s, d, np.concatenate(lab), 2)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_block_chains_split_with_inherited_passes(wcc, seed):
+    w = _block_chains(seed)
+    ref, rst, _, _ = _oracle(w)
+    assert rst["splits"] > 0
+    for mode in ("batched", "plain"):
+        out, st = _gpu(wcc, w, mode=mode)
+        assert np.array_equal(out, ref), mode
+        assert st["splits"] == rst["splits"] and st["peeled"] == rst["peeled"]
+
+
 def test_dc_planted_small(wcc):
     w = synth.dc_planted(200_000, 2_000_000, seed=5, size_max=5000)
     ref, _, _, _ = _oracle(w)
