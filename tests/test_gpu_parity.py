@@ -65,6 +65,35 @@ def test_csr_builder_matches_oracle(wcc):
     assert np.array_equal(goff, off) and np.array_equal(gadj, adj)
 
 
+@pytest.mark.parametrize("dups", [False, True])
+def test_csr_builder_rows_of_every_length(wcc, dups):
+    """Rows at the edges of the builder's three sorting classes (a warp for
+    at most 32 entries, a CTA in shared memory for at most 16384, one radix
+    sort over the longer rows), with and without duplicate, reversed and
+    self-loop edges, against the oracle's CSR."""
+    rng = np.random.default_rng(7 + dups)
+    n = 60_000
+    src, dst = [], []
+    for h, d in [(0, 40_000), (1, 16_385), (2, 16_384), (3, 16_383), (4, 33), (5, 32), (6, 31),
+                 (7, 1), (8, 20_000)]:
+        nb = rng.choice(np.arange(100, n), size=d, replace=False)
+        src.append(np.full(d, h)); dst.append(nb)
+    a = rng.integers(100, n, 200_000)
+    b = rng.integers(100, n, 200_000)
+    src.append(a); dst.append(b)
+    if dups:
+        src.append(b[:30_000]); dst.append(a[:30_000])           # reversed copies
+        src.append(np.arange(20)); dst.append(np.arange(20))     # self-loops
+        src.append(np.zeros(6000, np.int64)); dst.append(dst[0][:6000].copy())  # hub repeats
+        src.append(dst[1][:500].copy()); dst.append(np.ones(500, np.int64))
+    src = np.concatenate(src).astype(np.int32)
+    dst = np.concatenate(dst).astype(np.int32)
+    off, adj = oracle.build_csr(n, src, dst)
+    with wcc.WccGraph.from_edges(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), n) as g:
+        goff, gadj = g.csr()
+    assert np.array_equal(goff, off) and np.array_equal(gadj, adj)
+
+
 def test_planted_1k_all_modes(wcc):
     w = synth.planted_1k(0)
     ref, rst, _, _ = _oracle(w)
