@@ -546,7 +546,7 @@ Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int6
   std::unique_ptr<Graph> g(new Graph());
   g->device = current_device();
   g->n = n;
-  DevBuf bsrc, bdst;
+  DevBuf bsrc, bdst, bk, bk2, btemp, bkeep, bpos;
   const int32_t *d_src = src, *d_dst = dst;
   if (!on_device && m > 0) {
     int32_t *a = static_cast<int32_t *>(bsrc.ensure(4 * m));
@@ -556,11 +556,40 @@ Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int6
     d_src = a;
     d_dst = b;
   }
+  const int b = (int)std::max<int64_t>(1, bitlen_u64(n > 0 ? (uint64_t)(n - 1) : 0));
+  const int64_t n2 = 2 * m;
   int64_t *d_off = static_cast<int64_t *>(g->off.ensure(8 * (n + 1)));
   WCC_CUDA(cudaMemsetAsync(d_off, 0, 8 * (n + 1), s));
   int64_t nnz = 0;
   if (m > 0) {
-    nnz = build_csr_rows(d_src, d_dst, m, n, *g, s);
+    // the columns get room for every directed entry, so nothing has to be
+    // read back before the end: one read of {error, nnz} closes the build
+    uint64_t *k1 = static_cast<uint64_t *>(bk.ensure(8 * n2));
+    uint64_t *k2 = static_cast<uint64_t *>(bk2.ensure(8 * n2));
+    void *temp = btemp.ensure(std::max(radix_temp_bytes(n2), scan_temp_bytes(n + 1)) + 64);
+    uint32_t *keep = static_cast<uint32_t *>(bkeep.ensure(4 * (n2 + 2)));
+    uint32_t *pos = static_cast<uint32_t *>(bpos.ensure(4 * (n2 + 1)));
+    unsigned *d_err = keep + n2 + 1;
+    WCC_CUDA(cudaMemsetAsync(d_err, 0, 4, s));
+    k_edge_keys<<<blocks_for(m), TB, 0, s>>>(d_src, d_dst, m, n, b, k1, d_err); note_launch();
+    WCC_CUDA(cudaGetLastError());
+    uint64_t *sorted = k1;
+    // valid keys are (u << b) | v < 2^(2b) - 1 (u != v); dropped self-loops
+    // carry all ones, so sorting on the low 2b bits puts them last
+    if (radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, s)) sorted = k2;
+    k_unique_flags<<<blocks_for(n2), TB, 0, s>>>(sorted, n2, keep, ~0ull); note_launch();
+    exclusive_scan_u32(keep, pos, n2, pos + n2, temp, s);
+    int32_t *d_adj = static_cast<int32_t *>(g->adj.ensure(4 * n2));
+    k_compact_edges<<<blocks_for(n2), TB, 0, s>>>(sorted, keep, pos, n2, b, d_adj, d_off);
+    note_launch();
+    exclusive_scan_i64(d_off, d_off, n + 1, nullptr, temp, s);
+    WCC_CUDA(cudaGetLastError());
+    uint32_t tail[2] = {0, 0};
+    WCC_CUDA(cudaMemcpyAsync(&tail[0], d_err, 4, cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaMemcpyAsync(&tail[1], pos + n2, 4, cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaStreamSynchronize(s));
+    if (tail[0]) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
+    nnz = tail[1];
   } else {
     g->adj.ensure(4);
   }

@@ -73,14 +73,6 @@ struct Graph {
   DevBuf rb[16];
 };
 
-// ---- csr.cu ------------------------------------------------------------------
-// The symmetric CSR of m undirected edges (device src/dst) into g.off (n + 1
-// entries, zeroed by the caller) and g.adj: rows ascending, duplicates and
-// self-loops dropped.  Returns the number of directed entries; fails with
-// WCC_ERR_INVALID on an endpoint outside [0, n).  Synchronises s.
-int64_t build_csr_rows(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, Graph &g,
-                       cudaStream_t s);
-
 // ---- refine.cu -------------------------------------------------------------
 // Work item of the device queue.
 struct Item {

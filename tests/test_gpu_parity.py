@@ -67,10 +67,9 @@ def test_csr_builder_matches_oracle(wcc):
 
 @pytest.mark.parametrize("dups", [False, True])
 def test_csr_builder_rows_of_every_length(wcc, dups):
-    """Rows at the edges of the builder's three sorting classes (a warp for
-    at most 32 entries, a CTA in shared memory for at most 16384, one radix
-    sort over the longer rows), with and without duplicate, reversed and
-    self-loop edges, against the oracle's CSR."""
+    """Rows of 1, 31-33, 16383-16385, 20000 and 40000 entries (hubs among
+    short rows), with and without duplicate, reversed and self-loop edges,
+    against the oracle's CSR."""
     rng = np.random.default_rng(7 + dups)
     n = 60_000
     src, dst = [], []
