@@ -56,6 +56,30 @@ __global__ void k_job_slots(const QSlot *__restrict__ ring, const int32_t *__res
   for (int p = threadIdx.x; p < it.n; p += blockDim.x) slot[pool[it.vbeg + p]] = tag | (unsigned)p;
 }
 
+// *maxd = the largest member degree sum over the queued items [0, count).
+// One CTA per item.
+__global__ void k_job_dsum(const QSlot *__restrict__ items, const int32_t *__restrict__ pool,
+                           const int64_t *__restrict__ off, unsigned long long count,
+                           unsigned long long *maxd) {
+  __shared__ long long part[32];
+  const unsigned long long q = blockIdx.x;
+  if (q >= count) return;
+  const Item it = items[q].item;
+  long long d = 0;
+  for (int p = threadIdx.x; p < it.n; p += blockDim.x) {
+    const int32_t v = pool[it.vbeg + p];
+    d += off[v + 1] - off[v];
+  }
+  d = warp_sum(d);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long t = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) atomicMax(maxd, (unsigned long long)t);
+  }
+}
+
 void sizes_for(Job &j) {
   j.smem_bytes = refine_smem_bytes_config(j.device);
   j.grid = refine_max_ctas(j.device, j.smem_bytes);
@@ -324,10 +348,12 @@ Job *job_load(Graph *g, const char *path, cudaStream_t s) {
     if (n != g->n || nnz != g->nnz)
       fail(WCC_ERR_INVALID, "the job file belongs to another graph (vertex or edge count differs)");
     j->in_clusters = r.get<int64_t>();
-    j->max_n = r.get<int64_t>();
-    j->max_dsum = r.get<int64_t>();
+    // the stored largest item and degree sum are informational: the working
+    // memory is sized from the loaded items themselves below
+    (void)r.get<int64_t>();
+    (void)r.get<int64_t>();
     j->rule.kind = r.get<int32_t>();
-    j->min_size = r.get<int32_t>();
+    j->min_size = std::max<int32_t>(2, r.get<int32_t>());
     j->rule.num = r.get<int64_t>();
     j->rule.den = r.get<int64_t>();
     j->rule = checked_rule(&j->rule);
@@ -348,10 +374,17 @@ Job *job_load(Graph *g, const char *path, cudaStream_t s) {
     if (sum_m != M) fail(WCC_ERR_INVALID, "corrupt job file (member count)");
     members.resize((size_t)M);
     if (M) r.get(members.data(), 4 * (size_t)M);
-    for (int32_t v : members)
-      if (v < 0 || v >= n) fail(WCC_ERR_INVALID, "corrupt job file (vertex id)");
+    {
+      std::vector<uint8_t> seen((size_t)n, 0);
+      for (int32_t v : members) {
+        if (v < 0 || v >= n) fail(WCC_ERR_INVALID, "corrupt job file (vertex id)");
+        if (seen[v]++) fail(WCC_ERR_INVALID, "corrupt job file (a vertex listed twice)");
+      }
+    }
     lmin.resize((size_t)n);
     if (n) r.get(lmin.data(), 4 * (size_t)n);
+    for (int32_t x : lmin)
+      if (x < -1 || x >= n) fail(WCC_ERR_INVALID, "corrupt job file (cluster minimum)");
     const uint64_t want = r.h;
     uint64_t got = 0;
     if (fread(&got, 1, sizeof(got), f) != sizeof(got) || got != want)
@@ -362,12 +395,10 @@ Job *job_load(Graph *g, const char *path, cudaStream_t s) {
     j->device = g->device;
     j->n = n;
     j->pool_len = std::max<int64_t>(M, 1);
-    sizes_for(*j);
-    j->pool.ensure(4 * (size_t)j->pool_len);
-    alloc_common(*j);
     // the queue renumbered from 0, item lists packed in order
     std::vector<QSlot> q((size_t)P);
     int64_t at = 0;
+    j->max_n = 0;
     for (int64_t i = 0; i < P; ++i) {
       q[i].item.vbeg = at;
       q[i].item.n = sizes[i];
@@ -375,9 +406,26 @@ Job *job_load(Graph *g, const char *path, cudaStream_t s) {
       q[i].item.req = 0;
       q[i].seq = (uint64_t)i;
       at += sizes[i];
+      j->max_n = std::max<int64_t>(j->max_n, sizes[i]);
     }
+    j->pool.ensure(4 * (size_t)j->pool_len);
     if (M)
       WCC_CUDA(cudaMemcpyAsync(j->pool.p, members.data(), 4 * (size_t)M, cudaMemcpyHostToDevice, s));
+    j->max_dsum = 0;
+    if (P) {
+      DevBuf tq, td;
+      auto *dq = static_cast<QSlot *>(tq.ensure(sizeof(QSlot) * (size_t)P));
+      auto *dmax = static_cast<unsigned long long *>(td.ensure(8));
+      WCC_CUDA(cudaMemcpyAsync(dq, q.data(), sizeof(QSlot) * (size_t)P, cudaMemcpyHostToDevice, s));
+      WCC_CUDA(cudaMemsetAsync(dmax, 0, 8, s));
+      k_job_dsum<<<(unsigned)P, 256, 0, s>>>(dq, j->pool.as<int32_t>(), g->off.as<int64_t>(),
+                                             (unsigned long long)P, dmax);
+      note_launch();
+      WCC_CUDA(cudaGetLastError());
+      j->max_dsum = (int64_t)read_back(dmax, s);
+    }
+    sizes_for(*j);
+    alloc_common(*j);
     if (n) {
       WCC_CUDA(cudaMemcpyAsync(j->lmin.p, lmin.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s));
       WCC_CUDA(cudaMemsetAsync(j->slot.p, 0xff, 8 * (size_t)n, s));

@@ -81,3 +81,62 @@ def test_load_rejects_foreign_and_corrupt_files(wcc, tmp_path):
         bad.write_bytes(path.read_bytes()[:100])
         with pytest.raises(wcc.WccError):
             wcc.WccJob.load(g, bad)  # truncated
+
+
+def _fnv1a(data: bytes) -> int:
+    h = 1469598103934665603
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _parse(blob: bytes):
+    """Offsets of the fields of a job file (layout of wcc_job_save)."""
+    import struct
+    n = struct.unpack_from("<q", blob, 8)[0]
+    hdr = 8 + 5 * 8 + 2 * 4 + 2 * 8 + 7 * 8
+    P, M = struct.unpack_from("<qq", blob, hdr)
+    items = hdr + 16
+    members = items + 8 * P
+    lmin = members + 4 * M
+    return n, P, M, hdr, items, members, lmin
+
+
+def _reseal(body: bytearray) -> bytes:
+    import struct
+    return bytes(body) + struct.pack("<Q", _fnv1a(bytes(body)))
+
+
+def test_load_checks_contents_not_only_the_checksum(wcc, tmp_path):
+    import struct
+    w, ref = _case()
+    path = tmp_path / "queue.wccjob"
+    with wcc.WccGraph.from_edges(w.src, w.dst, w.n) as g:
+        with wcc.WccJob.start(g, w.labels, min_size=w.min_size) as job:
+            job.save(path)
+        blob = path.read_bytes()
+        body = bytearray(blob[:-8])
+        assert _reseal(body) == blob  # the test's reading of the format is the library's
+        n, P, M, hdr, items, members, lmin = _parse(blob)
+        assert P > 1 and M > 1
+        bad = tmp_path / "bad.wccjob"
+        # a vertex listed twice
+        b1 = bytearray(body)
+        b1[members + 4:members + 8] = b1[members:members + 4]
+        bad.write_bytes(_reseal(b1))
+        with pytest.raises(wcc.WccError):
+            wcc.WccJob.load(g, bad)
+        # a cluster minimum outside [-1, n)
+        b2 = bytearray(body)
+        struct.pack_into("<i", b2, lmin, n)
+        bad.write_bytes(_reseal(b2))
+        with pytest.raises(wcc.WccError):
+            wcc.WccJob.load(g, bad)
+        # a header that understates the largest item and degree sum: the
+        # working memory is sized from the items, so the run is unchanged
+        b3 = bytearray(body)
+        struct.pack_into("<qq", b3, 8 + 3 * 8, 1, 1)
+        bad.write_bytes(_reseal(b3))
+        with wcc.WccJob.load(g, bad) as job:
+            assert job.step(-1)
+            assert np.array_equal(job.finish(), ref)
