@@ -89,3 +89,20 @@ def test_reference_arm_prints_the_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_oracle_over_all_cores_leaves_no_process():
+    """The all-cores oracle figure: disjoint input clusters per spawned
+    process, a positive rate, and every worker gone afterwards."""
+    import multiprocessing as mp
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    w = synth.lfr_like(20_000, seed=0, min_size=2)
+    r = bench.cpu_baseline_pool(w, budget_s=1.0)
+    assert r["value"] > 0 and r["unit"] == "edges/s" and r["cores"] >= 1
+    assert not mp.active_children()
+    with pytest.raises(Exception):
+        bench.cpu_baseline_pool(w, timeout_s=0.001)  # workers cannot start in time
+    assert not mp.active_children()
