@@ -276,14 +276,24 @@ def cpu_baseline_pool(sw, budget_s: float = 8.0, timeout_s: float = 120.0):
             raise TimeoutError("oracle worker did not answer")
         return c.recv()
 
+    def send_quietly(c, obj):
+        try:
+            c.send(obj)
+        except (OSError, EOFError):
+            pass  # the worker is gone; its "ready" never comes
+
     try:
         for m in masks:
             a, b = ctx.Pipe()
             pr = ctx.Process(target=_pool_worker, args=(b,), daemon=True)
             pr.start()
+            b.close()  # the worker's end: a worker that dies closes the pipe
             procs.append(pr)
             conns.append(a)
-            a.send((off, adj, lab, int(sw.min_size), m))
+            # the arrays go from a thread, so that a worker that never reads
+            # cannot hold this one past the deadline below
+            threading.Thread(target=send_quietly, args=(a, (off, adj, lab, int(sw.min_size), m)),
+                             daemon=True).start()
         for c in conns:
             if recv(c) != "ready":
                 raise RuntimeError("oracle worker failed to start")
