@@ -219,7 +219,7 @@ def cpu_baseline(name, w, budget_s: float = 12.0):
                      f"mean {mean * 1e3:.1f} ms each",
            "clusters_per_s": k / mean}
     # the all-cores figure beside it, where a step is long enough to share out
-    if mean >= 0.02 and (os.cpu_count() or 1) > 1:
+    if mean >= 0.02 and host_cores() > 1:
         try:
             out["all_cores"] = cpu_baseline_pool(sw)
         except Exception as e:  # the single-core baseline stands on its own
@@ -228,6 +228,15 @@ def cpu_baseline(name, w, budget_s: float = 12.0):
 
 
 # ---- the oracle over disjoint sets of input clusters, one process each -----
+def host_cores() -> int:
+    """Cores this process may run on (its affinity mask), at most 64."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    return max(1, min(n, 64))
+
+
 def _pool_worker(conn):
     """Receives (off, adj, labels, min_size, mask) once, then times one oracle
     run over its input clusters per "run" message until "stop"."""
@@ -251,7 +260,7 @@ def cpu_baseline_pool(sw, budget_s: float = 8.0, timeout_s: float = 120.0):
     import multiprocessing as mp
     import numpy as np
     import oracle
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     lab = np.asarray(sw.labels)
     ok = lab >= 0
     nlab = int(lab[ok].max()) + 1 if ok.any() else 0
