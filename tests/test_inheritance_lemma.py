@@ -14,6 +14,7 @@ edges, split on the oracle's canonical cut, it checks the claim:
     in order, builds exactly the parent's sets restricted to it.
 """
 import numpy as np
+import pytest
 
 import oracle
 
@@ -91,12 +92,21 @@ def block_graph(rng):
     return n, (key // n).astype(np.int32), (key % n).astype(np.int32)
 
 
-def test_prefix_side_inherits_the_parent_first_pass():
+RULES = {"log10": (oracle.RULE_LOG10, 1, 1, 10), "log2": (oracle.RULE_LOG2, 1, 1, 5),
+         "sqrt": (oracle.RULE_SQRT, 1, 1, 0), "linear": (oracle.RULE_LINEAR, 1, 20, 0)}
+
+
+@pytest.mark.parametrize("rule", list(RULES))
+def test_prefix_side_inherits_the_parent_first_pass(rule):
+    # sqrt and linear thresholds change with almost every size, so a side
+    # rarely keeps its parent's kcap there and nothing is inherited; the
+    # no-crossing half of the lemma holds under every rule
+    kind, num, den, min_exercised = RULES[rule]
     rng = np.random.default_rng(2509)
     exercised = prefix_sides = differs_without_prefix = 0
     for _ in range(60):
         n0, eu0, ev0 = block_graph(rng)
-        alive = oracle.peel(n0, eu0, ev0)
+        alive = oracle.peel(n0, eu0, ev0, kind, num, den)
         ids = np.nonzero(alive)[0]
         loc = -np.ones(n0, np.int64)
         loc[ids] = np.arange(len(ids))
@@ -104,7 +114,7 @@ def test_prefix_side_inherits_the_parent_first_pass():
         n, eu, ev = len(ids), loc[eu0[m]], loc[ev0[m]]
         if n < 4 or oracle.components(n, eu, ev).max() > 0:
             continue
-        T = oracle.threshold(n)
+        T = oracle.threshold(n, kind, num, den)
         accepted, lam, side, _ = oracle.item_cut(n, eu.astype(np.int32), ev.astype(np.int32), T)
         if accepted:
             continue
@@ -136,9 +146,9 @@ def test_prefix_side_inherits_the_parent_first_pass():
             sl[members] = np.arange(size)
             inside = s[eu] & s[ev]
             su, sv = sl[eu[inside]], sl[ev[inside]]
-            if not oracle.peel(size, su.astype(np.int32), sv.astype(np.int32)).all():
+            if not oracle.peel(size, su.astype(np.int32), sv.astype(np.int32), kind, num, den).all():
                 continue
-            if oracle.threshold(size) != T:
+            if oracle.threshold(size, kind, num, den) != T:
                 continue
             exercised += 1
             cpos, csat = capped_pass(size, nbr_lists(size, su, sv), T + 1)
@@ -147,5 +157,5 @@ def test_prefix_side_inherits_the_parent_first_pass():
             child_sets = sets_of(size, su, sv, contracted(su, sv, cpos, csat))
             inherited = sl[parent_sets[members]]
             assert np.array_equal(child_sets, inherited)
-    assert prefix_sides >= 20 and exercised >= 10, (prefix_sides, exercised)
+    assert prefix_sides >= 20 and exercised >= min_exercised, (prefix_sides, exercised)
     assert differs_without_prefix >= 10, differs_without_prefix
