@@ -657,6 +657,16 @@ def main():
                 "ms_per_launch": r_ms, "share_of_step": r_ms / (total_ms / args.steps)}
     if name == "lfr_100k":
         roofline["traffic"] = profiled_traffic()
+    # the CSR build (a1) against the same peak: algorithmic bytes are the edge
+    # list read (8 B per edge) and the CSR written (int64 offsets, int32 columns)
+    if resident and resident.get("csr_build_ms"):
+        try:
+            c_bytes = 8.0 * w.m + 8.0 * (w.n + 1) + 4.0 * (2 * w.m)
+            c_gbs = c_bytes / (resident["csr_build_ms"] / 1e3) / 1e9
+            resident["csr_roofline"] = {"bound": "hbm", "alg_bytes": c_bytes, "achieved": c_gbs,
+                                        "peak": peak, "unit": "GB/s", "frac": c_gbs / peak}
+        except (TypeError, ValueError, ZeroDivisionError):
+            resident["csr_roofline"] = None
 
     serving = None
     if args.serving_requests > 0 and name == "lfr_100k":
