@@ -71,3 +71,87 @@ def min_labels(labels):
     for _, vs in clusters_of(labels).items():
         out[vs] = vs.min()
     return out
+
+
+# ---- capped maximum-adjacency passes, restated from their definition ----
+# (Nagamochi-Ibaraki with threshold k: keys capped at k, largest key first,
+# ties to the smallest id; an edge whose key reaches k is contracted.)  These
+# restate the contraction independently of the oracle and of the kernel.
+
+def nbr_lists(n, eu, ev):
+    """Neighbour lists with one entry per edge (repeated for parallel edges)."""
+    nb = [[] for _ in range(n)]
+    for x, y in zip(eu, ev):
+        nb[int(x)].append(int(y))
+        nb[int(y)].append(int(x))
+    return nb
+
+
+def capped_pass(n, nbrs, k):
+    """(pos, sat): pick step of every vertex and the step at which its key
+    reached k (n + 1 if never)."""
+    key = np.zeros(n, np.int64)
+    added = np.zeros(n, bool)
+    pos = np.full(n, -1, np.int64)
+    sat = np.full(n, n + 1, np.int64)
+    for step in range(n):
+        v = int(np.argmax(np.where(added, -1, key)))  # largest key, smallest id
+        added[v] = True
+        pos[v] = step
+        for u in nbrs[v]:
+            if not added[u] and key[u] < k:
+                key[u] += 1
+                if key[u] == k:
+                    sat[u] = step
+    return pos, sat
+
+
+def contracted(eu, ev, pos, sat):
+    """Mask of contracted edges: the later end's key had reached k by the
+    time the earlier end was picked."""
+    a = np.where(pos[eu] < pos[ev], eu, ev)
+    j = np.where(pos[eu] < pos[ev], ev, eu)
+    return sat[j] <= pos[a]
+
+
+def sets_of(n, eu, ev, mask):
+    """Smallest member of each vertex's set under the masked edges."""
+    p = np.arange(n)
+
+    def find(x):
+        while p[x] != x:
+            p[x] = p[p[x]]
+            x = p[x]
+        return x
+
+    for x, y in zip(eu[mask], ev[mask]):
+        rx, ry = find(int(x)), find(int(y))
+        if rx != ry:
+            p[max(rx, ry)] = min(rx, ry)
+    return np.array([find(x) for x in range(n)])
+
+
+def contract_passes(n, eu, ev, k):
+    """Passes of capped_pass on the contracted multigraph (super-vertices
+    renumbered 0.. in ascending order of their smallest member, which keeps
+    every tie) until one super-vertex is left or a pass contracts nothing.
+    Returns (rep, passes): rep[v] = smallest member of v's super-vertex."""
+    eu = np.asarray(eu, np.int64)
+    ev = np.asarray(ev, np.int64)
+    rep = np.arange(n)
+    passes = 0
+    while True:
+        svs = np.unique(rep)
+        if len(svs) <= 1:
+            break
+        idx = np.searchsorted(svs, rep)
+        qu, qv = idx[eu], idx[ev]
+        keep = qu != qv
+        qu, qv = qu[keep], qv[keep]
+        passes += 1
+        pos, sat = capped_pass(len(svs), nbr_lists(len(svs), qu, qv), k)
+        mask = contracted(qu, qv, pos, sat)
+        if not mask.any():
+            break
+        rep = svs[sets_of(len(svs), qu, qv, mask)[idx]]
+    return rep, passes

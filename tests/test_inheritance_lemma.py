@@ -6,9 +6,10 @@ things hold: S's members are positions 0 .. |S|-1 of the parent's
 first-pass order, nothing in S peels, and S has the parent's kcap.  This
 test restates the first pass (capped maximum-adjacency order, ties to the
 smallest id, an entry a -> j contracted iff j's key reached kcap no later
-than a's pick; Nagamochi-Ibaraki with k = T + 1) independently of both the
-kernel and the oracle.  On seeded graphs of dense blocks joined by a few
-edges, split on the oracle's canonical cut, it checks the claim:
+than a's pick; Nagamochi-Ibaraki with k = T + 1; tests/_helpers.py)
+independently of both the kernel and the oracle.  On seeded graphs of dense
+blocks joined by a few edges, split on the oracle's canonical cut, it checks
+the claim:
   * no contracted entry crosses the cut when a side is a prefix;
   * the side's own first pass, on its induced subgraph with ids renumbered
     in order, builds exactly the parent's sets restricted to it.
@@ -17,57 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
-
-
-def capped_pass(n, nbrs, k):
-    """(pos, sat): pick step of every vertex and the step at which its key
-    reached k (n + 1 if never)."""
-    key = np.zeros(n, np.int64)
-    added = np.zeros(n, bool)
-    pos = np.full(n, -1, np.int64)
-    sat = np.full(n, n + 1, np.int64)
-    for step in range(n):
-        v = int(np.argmax(np.where(added, -1, key)))  # largest key, smallest id
-        added[v] = True
-        pos[v] = step
-        for u in nbrs[v]:
-            if not added[u] and key[u] < k:
-                key[u] += 1
-                if key[u] == k:
-                    sat[u] = step
-    return pos, sat
-
-
-def contracted(eu, ev, pos, sat):
-    """Mask of contracted edges."""
-    a = np.where(pos[eu] < pos[ev], eu, ev)
-    j = np.where(pos[eu] < pos[ev], ev, eu)
-    return sat[j] <= pos[a]
-
-
-def sets_of(n, eu, ev, mask):
-    """Smallest member of each vertex's set under the masked edges."""
-    p = np.arange(n)
-
-    def find(x):
-        while p[x] != x:
-            p[x] = p[p[x]]
-            x = p[x]
-        return x
-
-    for x, y in zip(eu[mask], ev[mask]):
-        rx, ry = find(int(x)), find(int(y))
-        if rx != ry:
-            p[max(rx, ry)] = min(rx, ry)
-    return np.array([find(x) for x in range(n)])
-
-
-def nbr_lists(n, eu, ev):
-    nb = [[] for _ in range(n)]
-    for x, y in zip(eu, ev):
-        nb[int(x)].append(int(y))
-        nb[int(y)].append(int(x))
-    return nb
+from tests._helpers import capped_pass, contracted, nbr_lists, sets_of
 
 
 def block_graph(rng):

@@ -17,8 +17,8 @@ from scipy.sparse.csgraph import connected_components
 
 import oracle
 import synth
-from tests._helpers import (brute_min_cut, clusters_of, cut_value, induced_edges, is_connected,
-                            min_labels)
+from tests._helpers import (brute_min_cut, capped_pass, clusters_of, contract_passes, contracted,
+                            cut_value, induced_edges, is_connected, min_labels, nbr_lists, sets_of)
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_traced.json")))
 
@@ -235,6 +235,83 @@ def test_item_cut_decision_and_side_brute_force():
         bits = (small[:, None] >> np.arange(n)[None, :]) & 1
         assert np.all(bits == bits[:, rep])
     assert n_fail > 50 and n_acc > 50
+
+
+def _random_connected(rng, n_lo, n_hi):
+    while True:
+        n = int(rng.integers(n_lo, n_hi + 1))
+        if rng.random() < 0.5:
+            iu, ju = np.triu_indices(n, 1)
+            keep = rng.random(len(iu)) < rng.uniform(0.1, 0.7)
+            eu, ev = iu[keep], ju[keep]
+        else:  # dense blocks joined by a few edges, ids shuffled
+            sizes = rng.integers(3, max(4, n // 2), size=int(rng.integers(2, 5)))
+            n = int(sizes.sum())
+            starts = np.concatenate([[0], np.cumsum(sizes)])
+            eu, ev = [], []
+            for b, s in enumerate(sizes):
+                iu, ju = np.triu_indices(int(s), 1)
+                keep = rng.random(len(iu)) < rng.uniform(0.4, 0.9)
+                eu += list(starts[b] + iu[keep]); ev += list(starts[b] + ju[keep])
+                if b + 1 < len(sizes):
+                    for _ in range(int(rng.integers(1, 4))):
+                        eu.append(int(starts[b] + rng.integers(0, s)))
+                        ev.append(int(starts[b + 1] + rng.integers(0, sizes[b + 1])))
+            perm = rng.permutation(n)
+            eu, ev = perm[np.array(eu)], perm[np.array(ev)]
+            lo, hi = np.minimum(eu, ev), np.maximum(eu, ev)
+            key = np.unique(lo.astype(np.int64) * n + hi)
+            eu, ev = key // n, key % n
+        eu, ev = np.asarray(eu, np.int32), np.asarray(ev, np.int32)
+        if len(eu) and is_connected(n, eu, ev):
+            return n, eu, ev
+
+
+def test_item_cut_contraction_matches_restated_passes():
+    """The contraction the oracle's cut step ends with (rep) equals the
+    passes restated from their definition in tests/_helpers.py (capped
+    maximum-adjacency order from the smallest id, ties to the smallest id,
+    an edge contracted when the later end's key reached k = T+1 by the
+    earlier end's pick; repeated on the contracted multigraph until one
+    super-vertex is left or a pass contracts nothing).  A wrong tie rule in
+    any pass changes rep on some of these graphs."""
+    rng = np.random.default_rng(11)
+    n_multi = n_fail = 0
+    for trial in range(1200):
+        n, eu, ev = _random_connected(rng, 4, 40)
+        T = int(rng.integers(0, 6))
+        acc, lam, side, rep = oracle.item_cut(n, eu, ev, T)
+        want, passes = contract_passes(n, eu, ev, T + 1)
+        assert np.array_equal(rep, want), (trial, n, T)
+        assert acc == (len(np.unique(want)) == 1)
+        n_multi += passes >= 3
+        n_fail += not acc
+    assert n_multi >= 100 and n_fail >= 200, (n_multi, n_fail)
+
+
+def test_first_contraction_pass_sets_match_restatement():
+    """The oracle's contraction after a first pass that leaves one
+    super-vertex or merges nothing is exactly that first pass's sets, so on
+    those graphs rep equals the first pass restated alone (capped_pass,
+    contracted, sets_of)."""
+    rng = np.random.default_rng(12)
+    checked = 0
+    for _ in range(1500):
+        n, eu, ev = _random_connected(rng, 4, 30)
+        T = int(rng.integers(0, 5))
+        pos, sat = capped_pass(n, nbr_lists(n, eu, ev), T + 1)
+        mask = contracted(eu.astype(np.int64), ev.astype(np.int64), pos, sat)
+        first = sets_of(n, eu, ev, mask)
+        nsv = len(np.unique(first))
+        if nsv != 1 and mask.any():
+            # a second pass may merge more; it must only coarsen the first
+            _, _, _, rep = oracle.item_cut(n, eu, ev, T)
+            assert np.array_equal(rep[first], rep)
+            continue
+        _, _, _, rep = oracle.item_cut(n, eu, ev, T)
+        assert np.array_equal(rep, first)
+        checked += 1
+    assert checked >= 300, checked
 
 
 # ---------------------------------------------------------------- whole refinement
