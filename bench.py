@@ -396,6 +396,115 @@ def profiled_traffic():
         return None
 
 
+# ------------------------------------------------------------------ roofline
+# Algorithmic bytes (what the method must move at least, not what the
+# kernels happen to move):
+#   CSR build: the edge list read (8 B per edge), the CSR written (8 B per
+#     row offset, 4 B per directed entry);
+#   refinement kernel: 8 B per member of an input cluster (its row offsets)
+#     and 8 B per adjacency entry of every extracted item (the neighbour id
+#     and its label), counted by the kernel itself;
+#   a whole step: the CSR build, the labels read (4 B per vertex), the
+#     refinement kernel's bytes and the labels written (4 B per vertex).
+def csr_bytes(n, m):
+    return 8.0 * m + 8.0 * (n + 1) + 4.0 * (2 * m)
+
+
+def kernel_roofline(alg_bytes, ms, peak, peak_kind, step_ms):
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    return {"kernel": "k_refine", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": ms, "share_of_step": ms / step_ms}
+
+
+def step_roofline(n, m, refine_bytes, step_ms, peak):
+    b = csr_bytes(n, m) + 4.0 * n + refine_bytes + 4.0 * n
+    gbs = b / (step_ms / 1e3) / 1e9
+    return {"alg_bytes": b, "achieved": gbs, "unit": "GB/s", "frac": gbs / peak}
+
+
+def csr_roofline(n, m, ms, peak):
+    try:
+        b = csr_bytes(n, m)
+        gbs = b / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "alg_bytes": b, "achieved": gbs, "peak": peak, "unit": "GB/s",
+                "frac": gbs / peak}
+    except (TypeError, ValueError, ZeroDivisionError):
+        return None
+
+
+# ------------------------------------------------------------------ a large configuration
+def large_record(wcc, torch, dev, flush, stream, peak, peak_kind, name="dcpp_10m", steps=5,
+                 warmup=3, resident_runs=5):
+    """A bounded measurement of a large configuration beside the headline
+    workload: the same step (CSR build + refinement, inputs resident, L2
+    flushed before each), the refinement on a resident graph, the CSR build
+    alone and the rooflines, with the default schedule tuning."""
+    w = workload(name, 0)
+    src, dst, lab = w.src.to(dev), w.dst.to(dev), w.labels.to(dev)
+    out = torch.empty_like(lab)
+
+    def step():
+        g = wcc.WccGraph.from_edges(src, dst, w.n)
+        try:
+            _, st = g.run(lab, min_size=w.min_size, out=out, stats=True)
+        finally:
+            g.close()
+        return st
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    step_ms, r_ms, r_bytes = [], [], []
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        r_ms.append(st["ms_refine"])
+        r_bytes.append(st["alg_bytes"])
+    res_ms, csr_ms = [], None
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    a.record(stream)
+    g = wcc.WccGraph.from_edges(src, dst, w.n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    csr_ms = a.elapsed_time(b)
+    with g:
+        g.run(lab, min_size=w.min_size, out=out)
+        for k in range(resident_runs):
+            flush.fill_(k & 0xff)
+            a.record(stream)
+            g.run(lab, min_size=w.min_size, out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            res_ms.append(a.elapsed_time(b))
+    sm = sorted(step_ms)
+    mean = sum(step_ms) / len(step_ms)
+    rm = sum(res_ms) / len(res_ms)
+    rk = sum(r_ms) / len(r_ms)
+    rb = sum(r_bytes) / len(r_bytes)
+    k_in = n_clusters(w)
+    rec = {"workload": describe(name, w)["workload"], "n": int(w.n), "m": int(w.m),
+           "input_clusters": k_in, "steps": steps, "warmup": warmup, "ms_per_step": mean,
+           "p50_ms": sm[len(sm) // 2], "p99_ms": sm[-1],
+           "edges_per_s": w.m / (mean / 1e3), "clusters_per_s": k_in / (mean / 1e3),
+           "graph_resident": {"ms_per_run": rm, "edges_per_s": w.m / (rm / 1e3),
+                              "clusters_per_s": k_in / (rm / 1e3), "runs": len(res_ms)},
+           "csr_build_ms": csr_ms,
+           "roofline": kernel_roofline(rb, rk, peak, peak_kind, mean),
+           "step_roofline": step_roofline(w.n, w.m, rb, mean, peak),
+           "csr_roofline": csr_roofline(w.n, w.m, csr_ms, peak),
+           "tuning": wcc.get_tuning()}
+    del src, dst, lab, out, w
+    torch.cuda.empty_cache()
+    return rec
+
+
 # ------------------------------------------------------------------ ranks
 def aggregate_ranks(dist, torch, dev, total_ms: float, m: int, clusters: int):
     """Weak scaling across ranks: every rank refines its own instance with no
@@ -495,6 +604,8 @@ def main():
     ap.add_argument("--resident-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=240)
+    ap.add_argument("--no-large-record", action="store_true",
+                    help="skip the bounded 10M-vertex record beside the default workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -646,27 +757,24 @@ def main():
     # the result must match the device-buffer run
     ok = bool(torch.equal(out_h, ref_out.cpu()))
 
-    # roofline of the dominant kernel (the refinement kernel)
+    # roofline of the dominant kernel (the refinement kernel) and of the step
     peak, peak_kind = hbm_peak()
     r_ms = sum(refine_ms) / len(refine_ms)
     r_bytes = sum(refine_bytes) / len(refine_bytes)
-    achieved = r_bytes / (r_ms / 1e3) / 1e9
-    roofline = {"kernel": "k_refine", "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_kind, "alg_bytes_per_launch": r_bytes,
-                "ms_per_launch": r_ms, "share_of_step": r_ms / (total_ms / args.steps)}
+    roofline = kernel_roofline(r_bytes, r_ms, peak, peak_kind, total_ms / args.steps)
     if name == "lfr_100k":
         roofline["traffic"] = profiled_traffic()
-    # the CSR build (a1) against the same peak: algorithmic bytes are the edge
-    # list read (8 B per edge) and the CSR written (int64 offsets, int32 columns)
+    roofline["step"] = step_roofline(w.n, w.m, r_bytes, total_ms / args.steps, peak)
     if resident and resident.get("csr_build_ms"):
+        resident["csr_roofline"] = csr_roofline(w.n, w.m, resident["csr_build_ms"], peak)
+
+    # a bounded record of the 10M-vertex configuration beside the headline
+    large_rec = None
+    if name == "lfr_100k" and not args.no_large_record:
         try:
-            c_bytes = 8.0 * w.m + 8.0 * (w.n + 1) + 4.0 * (2 * w.m)
-            c_gbs = c_bytes / (resident["csr_build_ms"] / 1e3) / 1e9
-            resident["csr_roofline"] = {"bound": "hbm", "alg_bytes": c_bytes, "achieved": c_gbs,
-                                        "peak": peak, "unit": "GB/s", "frac": c_gbs / peak}
-        except (TypeError, ValueError, ZeroDivisionError):
-            resident["csr_roofline"] = None
+            large_rec = large_record(wcc, torch, dev, flush, stream, peak, peak_kind)
+        except Exception as e:  # the headline stands on its own
+            large_rec = {"error": f"{type(e).__name__}: {e}"[:300]}
 
     serving = None
     if args.serving_requests > 0 and name == "lfr_100k":
@@ -677,8 +785,9 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-                "config": describe(name, w) | {"mode": "batched", "parallelism": f"independent x{world}",
-                                               "tuning": tuning | {"autotuned": large}},
+                "config": describe(name, w),
+                "schedule": {"mode": "batched", "parallelism": f"independent x{world}",
+                             "tuning": tuning | {"autotuned": large}},
                 "clusters_per_s": clusters_per_s, "p50_ms": pct(step_ms, 0.5),
                 "p99_ms": pct(step_ms, 0.99),
                 "graph_resident": resident,
@@ -689,7 +798,7 @@ def main():
                         "d2h_bytes_per_step": int(4 * w.n), "ms_per_step": 1e3 * e2e_mean,
                         "steps": len(e2e_t), "matches_device_run": ok},
                 "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
-                "serving": serving}
+                "dcpp_10m": large_rec, "serving": serving}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(name, w)
         print(json.dumps(line), flush=True)

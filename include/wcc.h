@@ -88,8 +88,9 @@ typedef struct {
   int64_t ni_passes;     /* contraction passes (maximum-adjacency orderings) */
   int64_t sw_phases;     /* Stoer-Wagner phases */
   int64_t max_item;      /* largest input cluster refined (vertices) */
-  int64_t alg_bytes;     /* algorithmic HBM bytes of the run: 20 B per item member (id, row
-                          * bounds) plus 12 B per adjacency entry read (id, slot tag) */
+  int64_t alg_bytes;     /* algorithmic HBM bytes of the refinement's extractions: 8 B per
+                          * member of an input cluster (row offsets) plus 8 B per adjacency
+                          * entry of every extracted item (neighbour id and its label) */
   double ms_membership;  /* device time: grouping vertices by input label */
   double ms_refine;      /* device time: the refinement kernel(s) */
   double ms_output;      /* device time: numbering the accepted clusters */
@@ -204,13 +205,15 @@ void wcc_server_destroy(wcc_server *s);
  * outside [0, n).
  * Its working memory is one fixed array of about 6.5 MB in the library's
  * static device memory, present on every GPU that loads the library until
- * the process exits; the call itself performs no device allocation.  The
- * array is shared by all calls and keeps the last call's contents (each call
- * clears what it needs), so calls that may overlap on the GPU -- different
- * streams, or several host threads -- race and must be serialised by the
- * caller.  The first call on a device looks up the array's device address
- * (with that device current); make that first call before any stream
- * capture. */
+ * the process exits; the call itself performs no device allocation (see
+ * wcc_device_allocations).  The array's address is looked up on every call
+ * with the current device; `stream` must belong to that device, else
+ * WCC_ERR_INVALID.  The array is shared by all calls and keeps the last
+ * call's contents (each call clears what it needs), so calls that may
+ * overlap on the GPU -- different streams, or several host threads -- race
+ * and must be serialised by the caller.  The call reads two values back and
+ * synchronises `stream` before it returns, so it cannot be recorded into a
+ * CUDA graph (stream capture). */
 int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
                            int64_t *row_off, int32_t *cols, int64_t *nnz, void *stream);
 
@@ -228,7 +231,7 @@ int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, in
 typedef struct wcc_tuning {
   int32_t tiny_max;      /* 0..32 (0: no item runs on a single warp) */
   int32_t tiny_max_deg;  /* >= 0 */
-  int32_t dense_max;     /* 0..32 (0: always the sparse passes) */
+  int32_t dense_max;     /* 0..128 (0: always the sparse passes) */
   int32_t forest_min_n;  /* >= 0 (0: never) */
   int32_t smem_kb;       /* >= 0 (0: the largest a CTA can opt into) */
   int32_t reserved[3];   /* zero */
@@ -292,6 +295,11 @@ void wcc_job_destroy(wcc_job *job);
 /* Number of CUDA kernels this library has launched in this process so far
  * (instrumentation: lets a caller count the kernels of a timed region). */
 int64_t wcc_kernel_launches(void);
+
+/* Number of device allocations (cudaMalloc calls) this library has made in
+ * this process so far.  Freed blocks are cached and reused, so repeated
+ * calls of the same sizes usually add none; instrumentation only. */
+int64_t wcc_device_allocations(void);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char *wcc_last_error(void);

@@ -16,7 +16,7 @@ from ._binding import (WCC_MODE_BATCHED, WCC_MODE_PLAIN, WCC_RULE_LINEAR,  # noq
                        WCC_RULE_LOG2, WCC_RULE_LOG10, WCC_RULE_SQRT, WccError,
                        wcc_build_csr_no_alloc, wcc_create_graph,
                        wcc_create_graph_from_edges, wcc_destroy_graph, wcc_graph_export_csr,
-                       wcc_graph_nnz, wcc_graph_num_vertices, wcc_kernel_launches,
+                       wcc_graph_nnz, wcc_graph_num_vertices, wcc_kernel_launches, wcc_device_allocations,
                        wcc_last_error, wcc_poll, wcc_run, wcc_server_create,
                        wcc_server_destroy, wcc_submit, wcc_wait,
                        wcc_stats, wcc_threshold_rule, wcc_tuning, wcc_get_tuning,

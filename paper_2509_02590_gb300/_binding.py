@@ -98,6 +98,8 @@ def _load():
     L.wcc_build_csr_no_alloc.restype = c_int
     L.wcc_kernel_launches.argtypes = []
     L.wcc_kernel_launches.restype = i64
+    L.wcc_device_allocations.argtypes = []
+    L.wcc_device_allocations.restype = i64
     L.wcc_last_error.argtypes = []
     L.wcc_last_error.restype = ctypes.c_char_p
     tp = ctypes.POINTER(wcc_tuning)
@@ -172,6 +174,10 @@ def wcc_build_csr_no_alloc(src: int, dst: int, m: int, n: int, row_off: int, col
 
 def wcc_kernel_launches() -> int:
     return int(lib.wcc_kernel_launches())
+
+
+def wcc_device_allocations() -> int:
+    return int(lib.wcc_device_allocations())
 
 
 def wcc_last_error() -> str:

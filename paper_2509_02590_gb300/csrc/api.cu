@@ -25,6 +25,9 @@ static std::atomic<int64_t> g_launches{0};
 void note_launch(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+// Device allocations (cudaMalloc calls that succeeded) made by the library.
+static std::atomic<int64_t> g_allocs{0};
+
 // Process-wide cache of device blocks, per device and power-of-two size
 // class.  Every API call ends with a stream synchronisation, so a block that
 // a finished call released can be handed to the next call at once; a graph
@@ -100,6 +103,7 @@ void *DevBuf::ensure(size_t b) {
          "device allocation of " + std::to_string(want) + " bytes failed: " +
              cudaGetErrorString(e));
   }
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
   bytes = want;
   return p;
 }
@@ -133,7 +137,7 @@ uint64_t wait_limit_ns() {
 // The process-wide tuning (wcc_set_tuning / wcc_autotune / wcc_load_tuning);
 // an environment variable, when set, overrides its field.
 static std::mutex g_tune_mu;
-static wcc_tuning g_tune = {32, 1024, 32, 0, 0, {0, 0, 0}};
+static wcc_tuning g_tune = {32, 1024, 128, 0, 0, {0, 0, 0}};
 
 wcc_tuning current_tuning() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -145,7 +149,7 @@ void store_tuning(const wcc_tuning &t) {
 }
 bool tuning_valid(const wcc_tuning &t) {
   return t.tiny_max >= 0 && t.tiny_max <= 32 && t.tiny_max_deg >= 0 && t.dense_max >= 0 &&
-         t.dense_max <= 32 && t.forest_min_n >= 0 && t.smem_kb >= 0 && t.reserved[0] == 0 &&
+         t.dense_max <= 128 && t.forest_min_n >= 0 && t.smem_kb >= 0 && t.reserved[0] == 0 &&
          t.reserved[1] == 0 && t.reserved[2] == 0;
 }
 static long long env_or(const char *name, long long fallback) {
@@ -161,11 +165,11 @@ int forest_min_n_config() {
 }
 
 // Most super-vertices left after the first contraction pass that the dense
-// finish takes (WCC_DENSE_NSV, at most 32; 0 keeps every item on the sparse
+// finish takes (WCC_DENSE_NSV, at most 128; 0 keeps every item on the sparse
 // passes).
 int dense_max_config() {
   const long long v = env_or("WCC_DENSE_NSV", current_tuning().dense_max);
-  return (int)(v < 0 ? 0 : v > 32 ? 32 : v);
+  return (int)(v < 0 ? 0 : v > 128 ? 128 : v);
 }
 
 // Items of at most this many vertices (WCC_TINY_N, at most 32; 0 keeps every
@@ -304,7 +308,7 @@ void check_derr(unsigned err, const char *what) { check_device_error(err, what);
 
 
 // Writes the per-item profile of the last refinement as CSV (appending).
-void dump_item_profile(const RefineParams &p, const char *path, cudaStream_t s) {
+void dump_item_profile(const RefineParams &p, const char *path, int ctas, cudaStream_t s) {
   unsigned cnt = read_back(p.prof_count, s);
   if (cnt > p.prof_cap) cnt = p.prof_cap;
   std::vector<ItemProf> h(cnt);
@@ -324,6 +328,18 @@ void dump_item_profile(const RefineParams &p, const char *path, cudaStream_t s) 
             q.dt[0], q.dt[1], q.dt[2], q.dt[3], q.dt[4], q.dt[5], q.dt[6], q.dt[7], q.t_begin, q.t_end,
             q.dbg[0], q.dbg[1], q.dbg[2], q.dbg[3], q.forest, q.nsv1, q.forest_cycles, q.fdbg[0],
             q.fdbg[1], q.fdbg[2], q.fdbg[3], q.fdbg[4], q.fdbg[5]);
+  fclose(f);
+  if (ctas <= 0 || p.prof_cta == nullptr) return;
+  std::vector<CtaProf> c((size_t)ctas);
+  WCC_CUDA(cudaMemcpyAsync(c.data(), p.prof_cta, sizeof(CtaProf) * (size_t)ctas,
+                           cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaStreamSynchronize(s));
+  f = fopen((std::string(path) + ".cta").c_str(), "a");
+  if (!f) return;
+  fprintf(f, "cta,claim,tiny,cta_time,batches,tiny_items,cta_items\n");
+  for (int i = 0; i < ctas; ++i)
+    fprintf(f, "%d,%lld,%lld,%lld,%d,%d,%d\n", i, c[i].claim, c[i].tiny, c[i].cta, c[i].batches,
+            c[i].tiny_items, c[i].cta_items);
   fclose(f);
 }
 
@@ -438,12 +454,15 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     const char *prof_path = getenv("WCC_PROFILE_ITEMS");
     DevBuf prof_buf;
     const unsigned prof_cap = 1u << 20;
+    DevBuf prof_cta_buf;
     if (prof_path && *prof_path) {
       char *pb = static_cast<char *>(prof_buf.ensure(sizeof(ItemProf) * prof_cap + 64));
       p.prof = reinterpret_cast<ItemProf *>(pb + 64);
       p.prof_count = reinterpret_cast<unsigned *>(pb);
       p.prof_cap = prof_cap;
       WCC_CUDA(cudaMemsetAsync(pb, 0, 64, s));
+      p.prof_cta = static_cast<CtaProf *>(prof_cta_buf.ensure(sizeof(CtaProf) * (size_t)grid));
+      WCC_CUDA(cudaMemsetAsync(p.prof_cta, 0, sizeof(CtaProf) * (size_t)grid, s));
     }
     if (mode == WCC_MODE_BATCHED) {
       p.slab = static_cast<char *>(rb[R_SLAB].ensure(slab_bytes * (size_t)grid));
@@ -463,7 +482,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
         }
       }
     }
-    if (p.prof) dump_item_profile(p, prof_path, s);
+    if (p.prof) dump_item_profile(p, prof_path, mode == WCC_MODE_BATCHED ? grid : 0, s);
   }
   tm.mark(2, s);
   RunCounters hc{};
@@ -610,24 +629,18 @@ constexpr int64_t NOALLOC_MAX_VERTICES = 1 << 22;
 constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)6656 * 1024;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch on `dev`, looked up once per device
-// (with that device current) and cached.
-void *noalloc_scratch(int dev) {
-  static std::mutex mu;
-  static void *addr[64] = {nullptr};
-  if (dev < 0 || dev >= 64) fail(WCC_ERR_CUDA, "device ordinal out of range");
-  std::lock_guard<std::mutex> lk(mu);
-  if (!addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      (void)cudaGetLastError();
-      fail(WCC_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") +
-                             cudaGetErrorString(e));
-    }
-    addr[dev] = p;
+// Device address of g_noalloc_scratch on the current device.  It is looked
+// up on every call (a cheap driver query), so the address always belongs to
+// the context the work runs in, also after a cudaDeviceReset.
+void *noalloc_scratch() {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    (void)cudaGetLastError();
+    fail(WCC_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") +
+                           cudaGetErrorString(e));
   }
-  return addr[dev];
+  return p;
 }
 
 void build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
@@ -642,7 +655,16 @@ void build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64
   if (row_off == nullptr || nnz_out == nullptr || (m > 0 && (src == nullptr || dst == nullptr || cols == nullptr)))
     fail(WCC_ERR_INVALID, "wcc_build_csr_no_alloc: NULL buffer");
   const int dev = current_device();
-  char *base = static_cast<char *>(noalloc_scratch(dev));
+  if (s != nullptr) {
+    // the scratch address is the current device's: the stream must be too
+    int sdev = -1;
+    WCC_CUDA(cudaStreamGetDevice(s, &sdev));
+    if (sdev != dev)
+      fail(WCC_ERR_INVALID, "wcc_build_csr_no_alloc: the stream belongs to device " +
+                                std::to_string(sdev) + ", the current device is " +
+                                std::to_string(dev));
+  }
+  char *base = static_cast<char *>(noalloc_scratch());
   const int64_t n2 = 2 * m;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t cap2 = (size_t)(2 * NOALLOC_MAX_EDGES);
@@ -716,7 +738,7 @@ void autotune_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *ru
     };
     const Knob knobs[] = {{&wcc_tuning::tiny_max, {0, 16, 32}},
                           {&wcc_tuning::tiny_max_deg, {256, 1024, 4096}},
-                          {&wcc_tuning::dense_max, {16, 32}},
+                          {&wcc_tuning::dense_max, {32, 64, 128}},
                           {&wcc_tuning::smem_kb, {0, 160}},
                           {&wcc_tuning::forest_min_n, {0, 48}}};
     for (const Knob &k : knobs) {
@@ -900,6 +922,8 @@ int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, in
 }
 
 int64_t wcc_kernel_launches(void) { return launches_so_far(); }
+
+int64_t wcc_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 const char *wcc_last_error(void) { return g_last_error.c_str(); }
 

@@ -135,6 +135,14 @@ struct ItemProf {
   long long fdbg[6];  // forest test: BFS cycles, BFS levels, tree checks, extra trees, degree+contraction, relabel
 };
 
+// Per-CTA time split of one profiled run (clock64 cycles of thread 0).
+struct CtaProf {
+  long long claim;     // claiming and waiting for items
+  long long tiny;      // batches of items on single warps
+  long long cta;       // items on the whole CTA
+  int batches, tiny_items, cta_items, pad;
+};
+
 struct RefineParams {
   ReqCtx *reqs;               // request table (device)
   int *done_flags;            // optional, host-mapped: set to 1 when a request's last item ends
@@ -155,6 +163,7 @@ struct RefineParams {
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
   ItemProf *prof;             // optional per-item profile (NULL = off)
+  CtaProf *prof_cta;          // with prof: one entry per CTA
   unsigned prof_cap;
   unsigned *prof_count;
 };

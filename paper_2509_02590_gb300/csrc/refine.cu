@@ -87,6 +87,7 @@ struct Mem {
   int W, S;
   uint32_t *ebits;     // one bit per local adjacency entry
   IT *adj;
+  size_t smem_used;    // bytes of dynamic shared memory the item occupies
 };
 
 template <typename IT>
@@ -116,6 +117,7 @@ __device__ __forceinline__ Mem<IT> carve(char *base, int n, int64_t d) {
   m.ebits = (uint32_t *)take(4 * (size_t)((d + 31) / 32 + 1));
   m.adj = (IT *)take(sizeof(IT) * (size_t)d);
   m.vis = reinterpret_cast<uint32_t *>(m.E);
+  m.smem_used = 0;
   return m;
 }
 
@@ -142,7 +144,11 @@ __device__ __forceinline__ bool carve_hot(Mem<IT> &m, int n, int levels, size_t 
   h += align16(4 * (size_t)levels * (size_t)(m.W + m.S));
   m.vis = reinterpret_cast<uint32_t *>(h);
   h += align16(4 * (size_t)m.W);
-  if (hb + align16(4 * (size_t)(n + 1)) <= smem_bytes) m.off = reinterpret_cast<int32_t *>(h);
+  m.smem_used = hb;
+  if (hb + align16(4 * (size_t)(n + 1)) <= smem_bytes) {
+    m.off = reinterpret_cast<int32_t *>(h);
+    m.smem_used = hb + align16(4 * (size_t)(n + 1));
+  }
   return true;
 }
 
@@ -152,7 +158,7 @@ struct Sh {
   long long lscan[RW + 1];
   int go;
   int32_t i0;
-  unsigned long long u0;
+  unsigned long long u0, u1;
   int32_t ntouched;
   int32_t contracted;
   int32_t changed;
@@ -169,6 +175,8 @@ struct Sh {
   int32_t nb;
   int32_t duf[32];    // dense finish: merges of one pass (union-find over indices)
   uint32_t dside;     // dense finish: side of the minimum cut (mask of indices)
+  int32_t wduf[128], wgrp[128];  // wide dense finish: union-find, sets of initial indices
+  uint32_t wside[4];             // wide dense finish: side of the minimum cut
   int32_t dcut, dpasses, dphases;
 };
 
@@ -467,27 +475,45 @@ __device__ __forceinline__ int components_af(const Mem<IT> &m, int n, int32_t *f
 // tag[i] in [0, n) names the child of local vertex i (-1: none).  Every tag
 // with at least min_size members becomes a new queue item whose vertex list
 // (ascending) is written into the parent's pool range.  Uses C, D, E, F.
+// With keep_largest, the kept child with the most members (ties: smallest
+// tag) is not published: the caller refines it in place, and the children
+// that are published fill the front of the range.  Returns that child's tag
+// (-1: none) and, in *emitted, the members published ahead of it.
 template <typename IT>
-__device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCtx &R,
-                                              ReqCtx *Rg, uint16_t req, const Mem<IT> &m,
-                                              const int32_t *tag, int n, int64_t vbeg, Sh &sh,
-                                              uint16_t cflags = 0) {
+__device__ __forceinline__ int emit_children(const RefineParams &P, const ReqCtx &R,
+                                             ReqCtx *Rg, uint16_t req, const Mem<IT> &m,
+                                             const int32_t *tag, int n, int64_t vbeg, Sh &sh,
+                                             uint16_t cflags = 0, bool keep_largest = false,
+                                             int *emitted = nullptr) {
   int32_t *cnt = m.C, *cidx = m.D, *cbase = m.E, *run = m.F;
   for (int t = threadIdx.x; t < n; t += RB) cnt[t] = 0;
+  if (threadIdx.x == 0) sh.u1 = 0ull;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += RB)
     if (tag[i] >= 0) atomicAdd(&cnt[tag[i]], 1);
   __syncthreads();
+  if (keep_largest) {
+    unsigned long long best = 0ull;
+    for (int t = threadIdx.x; t < n; t += RB)
+      if (cnt[t] >= R.min_size) {
+        const unsigned long long pk = ((unsigned long long)cnt[t] << 32) | (unsigned)(0x7fffffff - t);
+        best = pk > best ? pk : best;
+      }
+    if (best) atomicMax(&sh.u1, best);
+    __syncthreads();
+  }
+  const int L = sh.u1 ? 0x7fffffff - (int)(unsigned)(sh.u1 & 0xffffffffull) : -1;
   for (int t = threadIdx.x; t < n; t += RB) {
-    bool keep = cnt[t] >= R.min_size;
+    bool keep = cnt[t] >= R.min_size && t != L;
     cidx[t] = keep ? 1 : 0;
     cbase[t] = keep ? cnt[t] : 0;
     run[t] = 0;
   }
   __syncthreads();
   int nchild = block_scan_array(cidx, n, sh);
-  block_scan_array(cbase, n, sh);
-  if (nchild == 0) return;
+  const int total = block_scan_array(cbase, n, sh);
+  if (emitted) *emitted = total;
+  if (nchild == 0) return L;
   if (threadIdx.x == 0) {
     add_ll(&Rg->pending, (long long)nchild);
     add_ll(&P.ctr->pending, (long long)nchild);
@@ -502,7 +528,7 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCt
     for (int b = 0; b < n; b += 32) {
       int i = b + lane;
       int t = i < n ? tag[i] : -1;
-      bool kept = t >= 0 && cnt[t] >= R.min_size;
+      bool kept = t >= 0 && t != L && cnt[t] >= R.min_size;
       int key = kept ? t : -1;
       unsigned peers = __match_any_sync(FULL, key);
       int rank = __popc(peers & lanemask_lt());
@@ -522,7 +548,7 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCt
   __threadfence();
   // descriptors, then publication
   for (int t = threadIdx.x; t < n; t += RB) {
-    if (cnt[t] < R.min_size) continue;
+    if (cnt[t] < R.min_size || t == L) continue;
     unsigned long long q = s0 + cidx[t];
     QSlot *sl = &P.ring[q % P.ring_cap];
     sl->item.vbeg = vbeg + cbase[t];
@@ -533,11 +559,26 @@ __device__ __forceinline__ void emit_children(const RefineParams &P, const ReqCt
   __threadfence();
   __syncthreads();
   for (int t = threadIdx.x; t < n; t += RB) {
-    if (cnt[t] < R.min_size) continue;
+    if (cnt[t] < R.min_size || t == L) continue;
     unsigned long long q = s0 + cidx[t];
     atomicExch((unsigned long long *)&P.ring[q % P.ring_cap].seq, q);
   }
   __syncthreads();
+  return L;
+}
+
+// Continues an item in place as its child L (the component labelled L in
+// tag): every other vertex becomes dead.  Returns the child's size.
+template <typename IT>
+__device__ __forceinline__ int restrict_alive(const Mem<IT> &m, const int32_t *tag, int L, int n,
+                                              Sh &sh) {
+  int c = 0;
+  for (int i = threadIdx.x; i < n; i += RB) {
+    const bool a = m.alive[i] && tag[i] == L;
+    m.alive[i] = a;
+    c += a;
+  }
+  return block_sum_int(c, sh);
 }
 
 // ---- maximum-adjacency machinery -----------------------------------------
@@ -1565,6 +1606,177 @@ __device__ DenseResult dense_finish(int32_t *w, int nsv, uint32_t live0, int kca
   return res;
 }
 
+// The same dense finish for up to DENSE_WIDE_NSV super-vertices: lane l
+// holds indices l, l+32, ... (K per lane); the merged sets are tracked in
+// grp[initial index] = the index that holds it now, and the minimum cut's
+// side is returned as a mask of initial indices (side[j], bit l = index
+// l + 32 j).  Same rules, same results, as dense_finish.
+constexpr int DENSE_WIDE_NSV = 128;
+
+template <int K>
+__device__ __forceinline__ bool dw_live(const uint32_t (&live)[K], int x) {
+  bool r = false;
+#pragma unroll
+  for (int j = 0; j < K; ++j) r = (x >> 5) == j ? ((live[j] >> (x & 31)) & 1u) != 0u : r;
+  return r;
+}
+
+template <int K>
+__device__ __forceinline__ void dw_kill(uint32_t (&live)[K], int x) {
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    if ((x >> 5) == j) live[j] &= ~(1u << (x & 31));
+}
+
+// Adds row and column x of w into r (r < x), zeroes r's diagonal, moves
+// x's members to r.  One warp.
+template <int K>
+__device__ __forceinline__ void dense_fold_w(int32_t *w, int nsv, int r, int x, int32_t *grp) {
+  const int c = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int cc = c + 32 * j;
+    if (cc < nsv) w[r * nsv + cc] += w[x * nsv + cc];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int cc = c + 32 * j;
+    if (cc < nsv) {
+      w[cc * nsv + r] += w[cc * nsv + x];
+      if (grp[cc] == x) grp[cc] = r;
+    }
+  }
+  __syncwarp();
+  if (c == 0) w[r * nsv + r] = 0;
+  __syncwarp();
+}
+
+template <int K>
+__device__ __forceinline__ void dense_order_w(const int32_t *w, int nsv, const uint32_t (&live)[K],
+                                              int kcap, int32_t *duf, int &s, int &t, int &cut,
+                                              bool &merged) {
+  const int l = threadIdx.x & 31;
+  long long key[K];
+  bool added[K];
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    key[j] = 0;
+    added[j] = !((live[j] >> l) & 1u);
+    cnt += __popc(live[j]);
+  }
+  s = t = -1;
+  cut = 0;
+  merged = false;
+  for (int step = 0; step < cnt; ++step) {
+    // largest key, ties to the smallest index
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const unsigned long long pk =
+          added[j] ? 0ull
+                   : (((unsigned long long)key[j] << 7) | (unsigned long long)(127 - (l + 32 * j))) + 1ull;
+      best = pk > best ? pk : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long x = __shfl_xor_sync(FULL, best, o);
+      best = x > best ? x : best;
+    }
+    const int X = 127 - (int)((best - 1ull) & 127ull);
+    s = t;
+    t = X;
+    cut = (int)((best - 1ull) >> 7);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int idx = l + 32 * j;
+      added[j] |= idx == X;
+      const int wx = idx < nsv ? w[X * nsv + idx] : 0;
+      if (!added[j] && wx > 0) {
+        long long nk = key[j] + wx;
+        if (kcap > 0 && nk >= kcap) {
+          nk = kcap;
+          volatile int32_t *vd = duf;
+          int a = X, b = idx;
+          for (;;) {
+            while (vd[a] != a) a = vd[a];
+            while (vd[b] != b) b = vd[b];
+            if (a == b) break;
+            if (a > b) { const int tt = a; a = b; b = tt; }
+            if (atomicCAS(&duf[b], b, a) == b) break;
+          }
+          merged = true;
+        }
+        key[j] = nk;
+      }
+    }
+    __syncwarp();
+  }
+  merged = __any_sync(FULL, merged);
+}
+
+// Every index 0..nsv-1 starts live.  duf, grp: nsv ints each; side: K words.
+template <int K>
+__device__ DenseResult dense_finish_w(int32_t *w, int nsv, int kcap, int32_t *duf, int32_t *grp,
+                                      uint32_t *side) {
+  const int l = threadIdx.x & 31;
+  uint32_t live[K];
+  int nlive = nsv;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const int b = 32 * j;
+    live[j] = nsv >= b + 32 ? FULL : (nsv > b ? (1u << (nsv - b)) - 1u : 0u);
+    if (l + b < nsv) grp[l + b] = l + b;
+  }
+  __syncwarp();
+  int passes = 0, phases = 0;
+  while (nlive > 1) {
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (l + 32 * j < nsv) duf[l + 32 * j] = l + 32 * j;
+    __syncwarp();
+    int s, t, cut;
+    bool merged;
+    dense_order_w<K>(w, nsv, live, kcap, duf, s, t, cut, merged);
+    ++passes;
+    if (!merged) break;
+    // fold every merged index into its root, in ascending order
+    volatile int32_t *vd = duf;
+    for (int x = 0; x < nsv; ++x) {
+      if (!dw_live<K>(live, x)) continue;
+      int r = x;
+      while (vd[r] != r) r = vd[r];
+      if (r == x) continue;
+      dense_fold_w<K>(w, nsv, r, x, grp);
+      dw_kill<K>(live, x);
+      --nlive;
+    }
+  }
+  DenseResult res{-1, 0u, passes, 0};
+  while (nlive > 1) {
+    int s, t, cut;
+    bool merged;
+    dense_order_w<K>(w, nsv, live, 0, duf, s, t, cut, merged);
+    ++phases;
+    if (res.cut < 0 || cut < res.cut) {
+      res.cut = cut;
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const unsigned b = __ballot_sync(FULL, l + 32 * j < nsv && grp[l + 32 * j] == t);
+        if (l == 0) side[j] = b;
+      }
+    }
+    const int lo = s < t ? s : t, hi = s < t ? t : s;
+    dense_fold_w<K>(w, nsv, lo, hi, grp);
+    dw_kill<K>(live, hi);
+    --nlive;
+  }
+  res.phases = phases;
+  __syncwarp();
+  return res;
+}
+
 template <typename IT>
 __device__ __forceinline__ void reset_ma_state(const Mem<IT> &m, int n) {
   for (int i = threadIdx.x; i < n; i += RB) {
@@ -1662,8 +1874,8 @@ __device__ __forceinline__ int tiny_components(uint32_t row, uint32_t set, uint3
 
 // Returns false, having done nothing, when the members' degree sum exceeds
 // P.tiny_max_deg (a hub's row would keep one warp busy while its CTA waits).
-__device__ bool tiny_item(const RefineParams &P, unsigned long long seq, const Item &it,
-                          int32_t *scratch) {
+__device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, const Item &it,
+                               int32_t *scratch) {
   const int l = threadIdx.x & 31;
   const int n = it.n;
   ReqCtx *Rg = &P.reqs[it.req];
@@ -1708,7 +1920,7 @@ __device__ bool tiny_item(const RefineParams &P, unsigned long long seq, const I
   }
   if (l == 0) {
     add_ll(&Rg->items, 1ll);
-    add_ll(&Rg->alg_bytes, 20ll * n + 12ll * D);
+    add_ll(&Rg->alg_bytes, ((it.flags & ITEM_TOP) ? 8ll * n : 0ll) + 8ll * D);
   }
   const uint32_t all = n >= 32 ? 0xffffffffu : (1u << n) - 1u;
   // 2. input cluster: CCR (Algorithm 1)
@@ -1772,6 +1984,39 @@ __device__ bool tiny_item(const RefineParams &P, unsigned long long seq, const I
   return true;
 }
 
+// tiny_item_body, recorded in the per-item profile when it is enabled
+// (outcome 100, no phase split).
+__device__ __forceinline__ bool tiny_item(const RefineParams &P, unsigned long long seq,
+                                          const Item &it, int32_t *scratch) {
+  if (!P.prof) return tiny_item_body(P, seq, it, scratch);
+  const long long t0 = (long long)globaltimer_ns();
+  const bool done = tiny_item_body(P, seq, it, scratch);
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0 && done) {
+    const unsigned r = atomicAdd(P.prof_count, 1u);
+    if (r < P.prof_cap) {
+      ItemProf *q = &P.prof[r];
+      q->seq = (unsigned)seq;
+      q->n = it.n;
+      q->E = q->nalive = q->passes = q->nsv = -1;
+      q->outcome = 100;
+      unsigned smid;
+      asm("mov.u32 %0, %%smid;" : "=r"(smid));
+      q->smid = (int)smid;
+      q->slab = 0;
+      q->top = (int)(it.flags & ITEM_TOP);
+      for (int z = 0; z < 8; ++z) q->dt[z] = 0;
+      q->t_begin = t0;
+      q->t_end = (long long)globaltimer_ns();
+      for (int z = 0; z < 4; ++z) q->dbg[z] = 0;
+      q->forest = q->nsv1 = 0;
+      q->forest_cycles = 0;
+      for (int z = 0; z < 6; ++z) q->fdbg[z] = 0;
+    }
+  }
+  return done;
+}
+
 // The end of an item: the request's and the run's pending counts drop (the
 // request's last item raises its host-mapped done flag).  One thread.
 __device__ __forceinline__ void finish_item(const RefineParams &P, uint16_t req) {
@@ -1799,6 +2044,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   const ReqCtx R = load_ctx(Rg);
   ReqCtx *ctr = Rg;  // per-request statistics (atomics)
   Mem<IT> m = carve<IT>(base, n, dbound);
+  if (SM) m.smem_used = ws_bytes<IT>(n, dbound);
   if (!SM) {
     const int64_t T0 = threshold_of(R.rule_kind, R.rule_num, R.rule_den, n);
     carve_hot(m, n, (int)(T0 + 2 < KB_LEVELS ? T0 + 2 : KB_LEVELS), P.smem_bytes);
@@ -1930,17 +2176,33 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   __syncthreads();
   if (threadIdx.x == 0) {
     add_ll(&ctr->items, 1ll);
-    add_ll(&ctr->alg_bytes, (long long)(4 * n + 16 * n + 12 * (long long)D));
+    // algorithmic bytes of the extraction: an input cluster reads its
+    // members' row offsets (8 B) and, per adjacency entry, the neighbour id
+    // and its label (4 + 4 B); re-inducing a part after a split reads the
+    // entries again (8 B each)
+    add_ll(&ctr->alg_bytes, (long long)((it.flags & ITEM_TOP) ? 8 * n : 0) + 8 * (long long)D);
     sh.pf_E = E;
   }
   prof_stamp(P, sh, 2);
+
+  // The item's vertices are the alive ones.  When it splits into components,
+  // the largest one with at least min_size vertices is not queued: this CTA
+  // continues with it in place (its induced subgraph is already here; it is
+  // the same child item, only without waiting behind the queue), and its
+  // later children go to the pool range vb behind the published ones.
+  int nalive = n;
+  int64_t vb = vbeg;
 
   // 2. input cluster: CCR (Algorithm 1)
   if (it.flags & ITEM_TOP) {
     int nc = components_af(m, n, m.B, m.H, sh);
     if (nc != 1) {
-      emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh);
-      return OUT_CCR_SPLIT;
+      int emitted = 0;
+      const int L = emit_children(P, R, Rg, it.req, m, m.B, n, vb, sh, 0, true, &emitted);
+      if (L < 0) return OUT_CCR_SPLIT;
+      nalive = restrict_alive(m, m.B, L, n, sh);
+      vb += emitted;
+      if (threadIdx.x == 0) add_ll(&ctr->items, 1ll);
     }
   }
   prof_stamp(P, sh, 3);
@@ -1949,7 +2211,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   int32_t *deg = m.A;
   for (int i = threadIdx.x; i < n; i += RB) deg[i] = m.off[i + 1] - m.off[i];
   __syncthreads();
-  int nalive = n;
+  const int n_item = nalive;
   for (;;) {
     const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, nalive);
     int rem = 0;
@@ -1969,7 +2231,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
     nalive -= rem;
   }
   if (threadIdx.x == 0) {
-    if (nalive < n) add_ll(&ctr->peeled, (long long)(n - nalive));
+    if (nalive < n_item) add_ll(&ctr->peeled, (long long)(n_item - nalive));
     sh.pf_nalive = nalive;
   }
   prof_stamp(P, sh, 4);
@@ -1977,12 +2239,18 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
 
   // 4. connectivity of what is left (an item arrives connected: input
   // clusters passed CCR above, children are components or sides of a
-  // minimum cut, which are connected; only a peel can disconnect it)
-  if (nalive < n) {
+  // minimum cut, which are connected; only a peel can disconnect it).  The
+  // component continued in place needs no peel of its own: T only grows
+  // with n, so every vertex left already has degree > T of its smaller size.
+  if (nalive < n_item) {
     int nc = components_af(m, n, m.B, m.H, sh);
     if (nc > 1) {
-      emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh);
-      return OUT_CC_SPLIT;
+      int emitted = 0;
+      const int L = emit_children(P, R, Rg, it.req, m, m.B, n, vb, sh, 0, true, &emitted);
+      if (L < 0) return OUT_CC_SPLIT;
+      nalive = restrict_alive(m, m.B, L, n, sh);
+      vb += emitted;
+      if (threadIdx.x == 0) add_ll(&ctr->items, 1ll);
     }
   }
   prof_stamp(P, sh, 5);
@@ -2073,10 +2341,21 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
       __syncthreads();
     }
     const long long tl0 = P.prof ? clock64() : 0;
-    if (bucketed && more && nsv > 1 && nsv <= P.dense_max && nsv * nsv <= 2 * (n + 1)) {
+    // the weight matrix of the dense finish: in E..F when it fits, else in
+    // the dynamic shared memory past what the item occupies
+    int32_t *wmat = nullptr;
+    if (nsv * nsv <= 2 * (n + 1)) {
+      wmat = reinterpret_cast<int32_t *>(m.wide);
+    } else {
+      const size_t at = align16(m.smem_used);
+      if (at + 4 * (size_t)nsv * (size_t)nsv <= P.smem_bytes)
+        wmat = reinterpret_cast<int32_t *>(wcc_dyn_smem + at);
+    }
+    if (bucketed && more && nsv > 1 && nsv <= P.dense_max && nsv <= DENSE_WIDE_NSV &&
+        wmat != nullptr) {
       // few super-vertices left: their weight matrix, then the dense finish
       int32_t *idx = m.C, *lr = m.D, *rank = m.H;
-      int32_t *w = reinterpret_cast<int32_t *>(m.wide);
+      int32_t *w = wmat;
       for (int i = threadIdx.x; i < n; i += RB) rank[i] = (m.alive[i] && rep[i] == i) ? 1 : 0;
       for (int q = threadIdx.x; q < nsv * nsv; q += RB) w[q] = 0;
       if (threadIdx.x == 0) sh.ntouched = 0;
@@ -2116,8 +2395,15 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
       }
       __syncthreads();
       if (threadIdx.x < 32) {
-        const DenseResult dr = dense_finish(w, nsv, nsv >= 32 ? 0xffffffffu : (1u << nsv) - 1u,
-                                            kcap, sh.duf);
+        DenseResult dr;
+        if (nsv <= DENSE_NSV) {
+          dr = dense_finish(w, nsv, nsv >= 32 ? 0xffffffffu : (1u << nsv) - 1u, kcap, sh.duf);
+          if (threadIdx.x == 0) sh.wside[0] = dr.side;
+        } else if (nsv <= 64) {
+          dr = dense_finish_w<2>(w, nsv, kcap, sh.wduf, sh.wgrp, sh.wside);
+        } else {
+          dr = dense_finish_w<4>(w, nsv, kcap, sh.wduf, sh.wgrp, sh.wside);
+        }
         if (threadIdx.x == 0) {
           sh.dcut = dr.cut;
           sh.dside = dr.side;
@@ -2135,9 +2421,10 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
         nsv = 1;
       } else {
         dense_cut = sh.dcut;
-        const uint32_t side = sh.dside;
-        for (int i = threadIdx.x; i < n; i += RB)
-          m.side[i] = m.alive[i] && ((side >> idx[rep[i]]) & 1u);
+        for (int i = threadIdx.x; i < n; i += RB) {
+          const int k = m.alive[i] ? idx[rep[i]] : 0;
+          m.side[i] = m.alive[i] && ((sh.wside[k >> 5] >> (k & 31)) & 1u);
+        }
         __syncthreads();
       }
       more = false;
@@ -2225,7 +2512,7 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (threadIdx.x == 0) add_ll(&ctr->splits, 1ll);
   for (int i = threadIdx.x; i < n; i += RB) m.B[i] = m.alive[i] ? (m.side[i] ? 1 : 0) : -1;
   __syncthreads();
-  emit_children(P, R, Rg, it.req, m, m.B, n, vbeg, sh, inh_valid ? ITEM_INH : (uint16_t)0);
+  emit_children(P, R, Rg, it.req, m, m.B, n, vb, sh, inh_valid ? ITEM_INH : (uint16_t)0);
   return OUT_CUT_SPLIT;
 }
 
@@ -2274,6 +2561,8 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
   volatile RunCounters *vctr = ctr;
   const bool tiny_ok = P.tiny_max > 0 && P.smem_bytes >= (size_t)RW * TINY_SCRATCH;
   bool took = false;  // thread 0: this CTA has claimed an item in this launch
+  CtaProf cp{0, 0, 0, 0, 0, 0, 0};  // thread 0, profile only
+  long long pc = P.prof ? clock64() : 0;
   for (;;) {
     if (threadIdx.x == 0) {
       int go = 0;
@@ -2394,6 +2683,11 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
       sh.go = go;
     }
     __syncthreads();
+    if (P.prof && threadIdx.x == 0) {
+      const long long t = clock64();
+      cp.claim += t - pc;
+      pc = t;
+    }
     if (!sh.go) break;
     const int nb = sh.nb;
     if (threadIdx.x == 0) sh.ntouched = 0;  // bit k: batch item k runs on the CTA
@@ -2411,6 +2705,14 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
         }
       }
       __syncthreads();
+      if (P.prof && threadIdx.x == 0) {
+        const long long t = clock64();
+        cp.tiny += t - pc;
+        pc = t;
+        ++cp.batches;
+        for (int k = 0; k < nb; ++k)
+          cp.tiny_items += (sh.batch[k].n <= P.tiny_max && !((sh.ntouched >> k) & 1)) ? 1 : 0;
+      }
     }
     const int cta_mask = sh.ntouched;
     for (int k = 0; k < nb; ++k) {
@@ -2463,9 +2765,16 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
       }
       if (threadIdx.x == 0) finish_item(P, it.req);
       __syncthreads();
+      if (P.prof && threadIdx.x == 0) {
+        const long long t = clock64();
+        cp.cta += t - pc;
+        pc = t;
+        ++cp.cta_items;
+      }
     }
     if (P.single_item) break;
   }
+  if (P.prof && P.prof_cta && threadIdx.x == 0) P.prof_cta[blockIdx.x] = cp;
 }
 
 }  // namespace

@@ -7,8 +7,9 @@ input clusters -- the largest ones, chain clusters (the ones that split) and
 a seeded random set -- the oracle runs on the induced subgraphs alone, with
 vertex ids renumbered monotonically (which keeps every tie-break), and the
 GPU result restricted to those vertices must be the same partition.  The
-2B-edge case needs about 100 GB of device memory and runs only when
-WCC_TEST_2B=1.
+2B-edge case needs about 100 GB of device memory.  The 10M-vertex graph is
+also refined repeatedly, through device and host buffers, and every result
+must be the same.
 """
 import os
 
@@ -72,10 +73,19 @@ def _wcc():
     return wcc
 
 
-def test_dcpp_10m_sampled_parity():
-    wcc = _wcc()
+@pytest.fixture(scope="module")
+def dcpp10m():
+    _wcc()
     from synth import gpu_graphs
     w = gpu_graphs.dcpp_10m(seed=0)
+    yield w
+    del w
+    torch.cuda.empty_cache()
+
+
+def test_dcpp_10m_sampled_parity(dcpp10m):
+    wcc = _wcc()
+    w = dcpp10m
     assert w.n == 10_000_000 and 190_000_000 < w.m < 210_000_000
     ref, got, ost, st, ns = _sampled_parity(wcc, w)
     assert st["in_clusters"] == w.meta["clusters"]
@@ -83,11 +93,41 @@ def test_dcpp_10m_sampled_parity():
     assert np.array_equal(got, ref), f"{int((got != ref).sum())} of {ns} sampled vertices differ"
 
 
-@pytest.mark.skipif(os.environ.get("WCC_TEST_2B") != "1", reason="set WCC_TEST_2B=1 (about 100 GB)")
-def test_dcpp_100m_sampled_parity():
+def test_dcpp_10m_repeated_runs_identical(dcpp10m):
+    """The refined clustering of the 10M-vertex graph is the same in every
+    run: five runs with device buffers on one graph, two with host buffers
+    on it, and two on a graph built again from the edge list copied from
+    pinned host memory (the end-to-end path), run with host buffers."""
     wcc = _wcc()
+    w = dcpp10m
+    with wcc.WccGraph.from_edges(w.src, w.dst, w.n) as g:
+        first = g.run(w.labels, min_size=w.min_size)
+        for _ in range(4):
+            assert torch.equal(g.run(w.labels, min_size=w.min_size), first)
+        ref = first.cpu().numpy()
+        lab_h = w.labels.cpu().numpy()
+        for _ in range(2):
+            assert np.array_equal(g.run(lab_h, min_size=w.min_size), ref)
+    src_h, dst_h = w.src.cpu().pin_memory(), w.dst.cpu().pin_memory()
+    lab_p = w.labels.cpu().pin_memory()
+    out_p = torch.empty_like(lab_p).pin_memory()
+    for _ in range(2):
+        with wcc.WccGraph.from_edges(src_h, dst_h, w.n) as g:
+            g.run(lab_p, min_size=w.min_size, out=out_p)
+        assert np.array_equal(out_p.numpy(), ref)
+
+
+def test_dcpp_100m_sampled_parity():
+    """About 100 GB of device memory: the 2B-edge graph, its CSR and the
+    refinement's working memory."""
+    wcc = _wcc()
+    free, _ = torch.cuda.mem_get_info()
+    if free < (150 << 30):
+        pytest.skip(f"needs about 150 GB of free device memory ({free >> 30} GB free)")
     from synth import gpu_graphs
     w = gpu_graphs.dcpp_100m(seed=0)
     assert w.n == 100_000_000 and 1_900_000_000 < w.m < 2_100_000_000
     ref, got, ost, st, ns = _sampled_parity(wcc, w, n_largest=2, n_chains=30, n_random=300)
     assert np.array_equal(got, ref), f"{int((got != ref).sum())} of {ns} sampled vertices differ"
+    del w
+    torch.cuda.empty_cache()

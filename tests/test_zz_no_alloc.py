@@ -55,20 +55,22 @@ def test_no_alloc_csr_matches_existing_entry_point():
         assert np.array_equal(off, ref_off)
         assert np.array_equal(adj, ref_adj)
 
-    # later calls add no device allocation
-    torch.cuda.synchronize()
-    free_before = torch.cuda.mem_get_info()[0]
+    # later calls make no device allocation: the library's own count of
+    # cudaMalloc calls does not move, and neither does the free memory
     s = torch.from_numpy(small.src).cuda()
     d = torch.from_numpy(small.dst).cuda()
     row_off = torch.empty(small.n + 1, dtype=torch.int64, device="cuda")
     cols = torch.empty(2 * small.m, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
     free_before = torch.cuda.mem_get_info()[0]
+    allocs_before = _binding.wcc_device_allocations()
     for _ in range(3):
         _binding.wcc_build_csr_no_alloc(s.data_ptr(), d.data_ptr(), small.m, small.n,
                                         row_off.data_ptr(), cols.data_ptr(),
                                         torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
+    assert allocs_before > 0  # the count is live: the graphs built above allocated
+    assert _binding.wcc_device_allocations() == allocs_before
     assert torch.cuda.mem_get_info()[0] == free_before
 
 
