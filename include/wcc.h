@@ -154,8 +154,10 @@ void wcc_destroy_graph(wcc_graph *g);
  * others are on the GPU joins the running kernel at once (its work overlaps
  * theirs).  Every result equals what wcc_run returns for the same input.
  * The server takes the device current at wcc_server_create; every graph
- * submitted must live on that device and stay alive (not destroyed) until
- * its request has been collected by wcc_poll / wcc_wait. */
+ * submitted with wcc_submit must live on that device and stay alive (not
+ * destroyed) until its request has been collected by wcc_poll / wcc_wait.
+ * wcc_submit_edges hands the server an edge list instead: the server then
+ * builds, keeps and releases the request's graph itself. */
 
 /* Create a server using at most mem_budget_bytes of device memory for its
  * queue, slabs and admitted requests.  WCC_ERR_INVALID if the budget cannot
@@ -168,6 +170,33 @@ int wcc_server_create(int64_t mem_budget_bytes, wcc_server **out);
  * can never fit the server's budget or queue. */
 int wcc_submit(wcc_server *s, const wcc_graph *g, const int32_t *clustering_in,
                const wcc_threshold_rule *rule, int32_t min_size, uint64_t *ticket);
+
+/* Queue a refinement of a graph given as an edge list: src[m], dst[m] (host,
+ * int32 ids in [0, n)) on n vertices, with clustering_in[n] (host), rule and
+ * min_size as in wcc_run.  All three buffers are copied before the call
+ * returns.  The server builds the graph on the device when it admits the
+ * request (both directions, self-loops and repeated edges dropped, as
+ * wcc_create_graph_from_edges) and releases it when the request finishes;
+ * the graph's CSR counts against the budget for the request's lifetime, the
+ * builder's transient memory during the admission.  An id outside [0, n)
+ * fails the request (WCC_ERR_INVALID from wcc_poll / wcc_wait).
+ * WCC_ERR_BUSY when the request can never fit the budget or queue. */
+int wcc_submit_edges(wcc_server *s, const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                     const int32_t *clustering_in, const wcc_threshold_rule *rule,
+                     int32_t min_size, uint64_t *ticket);
+
+/* Admission counters of a server (instrumentation). */
+typedef struct {
+  int64_t budget_bytes;     /* budget left for requests after the fixed structures */
+  int64_t used_bytes;       /* held by the requests admitted now */
+  int64_t peak_used_bytes;  /* most ever held at once (with a build's transient memory) */
+  int64_t admitted;         /* requests admitted so far */
+  int64_t budget_waits;     /* requests that had to wait for budget before admission */
+  int64_t slot_waits;       /* admission attempts that found every request slot taken */
+  int64_t peak_active;      /* most requests admitted at once */
+  int64_t max_active;       /* request slots */
+} wcc_server_counters;
+int wcc_server_info(wcc_server *s, wcc_server_counters *out);
 
 /* Non-blocking: WCC_PENDING while the request runs; WCC_OK once finished,
  * with the result written to the host buffer clustering_out[n] (numbered as
@@ -291,6 +320,31 @@ int wcc_job_load(const wcc_graph *g, const char *path, void *stream, wcc_job **o
 int wcc_job_finish(wcc_job *job, int32_t *clustering_out, int on_device, void *stream,
                    wcc_stats *stats);
 void wcc_job_destroy(wcc_job *job);
+
+/* ---- one graph's input clusters refined on several GPUs -----------------
+ * Algorithms 1-2 refine every input cluster on its own (Section 2.2-2.3), so
+ * the input clusters of one graph can be split into disjoint shards, one
+ * per GPU, each refined with wcc_run on a full copy of the graph (labels of
+ * other shards set to -1).  The shard results are merged through cluster
+ * minima: per vertex, the smallest vertex id of its output cluster.  The
+ * shards' minima arrays are disjoint (-1 outside the shard), so their
+ * element-wise maximum (one all-reduce) is the minima of the whole run, and
+ * wcc_number_by_minima numbers it exactly as a single wcc_run would. */
+
+/* Per vertex v, the smallest vertex id of v's cluster: labels[n] (host or
+ * device per on_device, int32 in [-1, n), -1 = no cluster, e.g. the output
+ * of wcc_run) -> minima[n] (-1 where labels is -1).  A label outside
+ * [-1, n) returns WCC_ERR_INVALID. */
+int wcc_cluster_minima(const int32_t *labels, int64_t n, int32_t *minima, int on_device,
+                       void *stream);
+
+/* Canonical numbering from cluster minima (as wcc_cluster_minima writes
+ * them): labels_out[n] gets 0..K-1 in ascending order of each cluster's
+ * smallest vertex and -1 where minima is -1, the numbering of wcc_run; *k
+ * (nullable) receives K.  Every entry must be -1 or a vertex r <= v with
+ * minima[r] == r, else WCC_ERR_INVALID. */
+int wcc_number_by_minima(const int32_t *minima, int64_t n, int32_t *labels_out, int64_t *k,
+                         int on_device, void *stream);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (instrumentation: lets a caller count the kernels of a timed region). */

@@ -134,7 +134,8 @@ class WccServer:
     """A continuous-batching refinement server (owns a ``wcc_server``).
 
     Requests carry host (numpy) clusterings; results come back as numpy
-    arrays.  A graph must stay open until its requests are collected."""
+    arrays.  A graph passed to ``submit`` must stay open until its requests
+    are collected; ``submit_edges`` hands the server an edge list instead."""
 
     def __init__(self, mem_budget_bytes: int):
         self.handle = wcc_server_create(int(mem_budget_bytes))
@@ -149,6 +150,24 @@ class WccServer:
                        min_size)
         self._n[t] = graph.n
         return t
+
+    def submit_edges(self, src, dst, n: int, labels, min_size: int = 2, rule="log10",
+                     num: int = 1, den: int = 1) -> int:
+        """Queue a request that brings its graph as a host edge list; the
+        server builds the graph on admission and releases it afterwards."""
+        s = np.ascontiguousarray(src, dtype=np.int32)
+        d = np.ascontiguousarray(dst, dtype=np.int32)
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        if len(s) != len(d) or len(lab) != n:
+            raise ValueError("src and dst must match; labels must have one entry per vertex")
+        t = _binding.wcc_submit_edges(self.handle, s.ctypes.data, d.ctypes.data, len(s), int(n),
+                                      lab.ctypes.data, rule_struct(rule, num, den), min_size)
+        self._n[t] = int(n)
+        return t
+
+    def info(self) -> dict:
+        """Admission counters (budget, bytes held, waits, requests at once)."""
+        return _binding.wcc_server_info(self.handle)
 
     def _collect(self, fn, ticket, *args):
         n = self._n[ticket]

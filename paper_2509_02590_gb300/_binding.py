@@ -53,6 +53,15 @@ class wcc_tuning(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
 
 
+class wcc_server_counters(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "budget_bytes", "used_bytes", "peak_used_bytes", "admitted", "budget_waits", "slot_waits",
+        "peak_active", "max_active")]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
 class WccError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -100,6 +109,16 @@ def _load():
     L.wcc_kernel_launches.restype = i64
     L.wcc_device_allocations.argtypes = []
     L.wcc_device_allocations.restype = i64
+    L.wcc_submit_edges.argtypes = [vp, vp, vp, i64, i64, vp,
+                                   ctypes.POINTER(wcc_threshold_rule), i32,
+                                   ctypes.POINTER(ctypes.c_uint64)]
+    L.wcc_submit_edges.restype = c_int
+    L.wcc_server_info.argtypes = [vp, ctypes.POINTER(wcc_server_counters)]
+    L.wcc_server_info.restype = c_int
+    L.wcc_cluster_minima.argtypes = [vp, i64, vp, c_int, vp]
+    L.wcc_cluster_minima.restype = c_int
+    L.wcc_number_by_minima.argtypes = [vp, i64, vp, ctypes.POINTER(i64), c_int, vp]
+    L.wcc_number_by_minima.restype = c_int
     L.wcc_last_error.argtypes = []
     L.wcc_last_error.restype = ctypes.c_char_p
     tp = ctypes.POINTER(wcc_tuning)
@@ -146,6 +165,21 @@ def wcc_submit(server: int, g: int, clustering_in: int, rule: wcc_threshold_rule
     return int(t.value)
 
 
+def wcc_submit_edges(server: int, src: int, dst: int, m: int, n: int, clustering_in: int,
+                     rule: wcc_threshold_rule | None, min_size: int) -> int:
+    t = ctypes.c_uint64(0)
+    _check(lib.wcc_submit_edges(server, src, dst, m, n, clustering_in,
+                                ctypes.byref(rule) if rule is not None else None, min_size,
+                                ctypes.byref(t)))
+    return int(t.value)
+
+
+def wcc_server_info(server: int) -> dict:
+    c = wcc_server_counters()
+    _check(lib.wcc_server_info(server, ctypes.byref(c)))
+    return c.as_dict()
+
+
 def wcc_poll(server: int, ticket: int, clustering_out: int,
              stats: wcc_stats | None = None) -> int:
     """WCC_OK or WCC_PENDING (raises on the request's error)."""
@@ -178,6 +212,17 @@ def wcc_kernel_launches() -> int:
 
 def wcc_device_allocations() -> int:
     return int(lib.wcc_device_allocations())
+
+
+def wcc_cluster_minima(labels: int, n: int, minima: int, on_device: int, stream: int) -> None:
+    _check(lib.wcc_cluster_minima(labels, n, minima, on_device, stream))
+
+
+def wcc_number_by_minima(minima: int, n: int, labels_out: int, on_device: int,
+                         stream: int) -> int:
+    k = ctypes.c_int64(0)
+    _check(lib.wcc_number_by_minima(minima, n, labels_out, ctypes.byref(k), on_device, stream))
+    return int(k.value)
 
 
 def wcc_last_error() -> str:

@@ -557,8 +557,8 @@ Graph *create_from_csr(const int64_t *off, const int32_t *adj, int64_t n, int64_
   return g.release();
 }
 
-Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
-                         int on_device, cudaStream_t s) {
+Graph *build_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                        int on_device, cudaStream_t s) {
   if (n < 0 || n >= (1ll << 31) - 1) fail(WCC_ERR_INVALID, "n must be in [0, 2^31-1)");
   if (m < 0 || 2 * m >= (1ll << 32)) fail(WCC_ERR_INVALID, "m must be in [0, 2^31)");
   if (m > 0 && (src == nullptr || dst == nullptr)) fail(WCC_ERR_INVALID, "src/dst is NULL");
@@ -844,6 +844,12 @@ int guarded(F &&f) {
 }
 
 }  // namespace
+
+Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                         int on_device, cudaStream_t s) {
+  return build_from_edges(src, dst, m, n, on_device, s);
+}
+
 }  // namespace wccg
 
 
@@ -918,6 +924,64 @@ int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, in
                            int64_t *row_off, int32_t *cols, int64_t *nnz, void *stream) {
   return guarded([&] {
     build_csr_no_alloc(src, dst, m, n, row_off, cols, nnz, (cudaStream_t)stream);
+  });
+}
+
+int wcc_cluster_minima(const int32_t *labels, int64_t n, int32_t *minima, int on_device,
+                       void *stream) {
+  return guarded([&] {
+    if (n < 0 || n >= (1ll << 31) - 1) fail(WCC_ERR_INVALID, "n must be in [0, 2^31-1)");
+    if (n > 0 && (labels == nullptr || minima == nullptr)) fail(WCC_ERR_INVALID, "NULL buffer");
+    current_device();
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws;
+    DevBuf din, dout;
+    const int32_t *l = labels;
+    int32_t *o = minima;
+    if (!on_device && n > 0) {
+      int32_t *t = static_cast<int32_t *>(din.ensure(4 * n));
+      WCC_CUDA(cudaMemcpyAsync(t, labels, 4 * n, cudaMemcpyHostToDevice, s));
+      l = t;
+      o = static_cast<int32_t *>(dout.ensure(4 * n));
+    }
+    cluster_minima(l, n, o, ws, s);
+    if (!on_device && n > 0) {
+      WCC_CUDA(cudaMemcpyAsync(minima, o, 4 * n, cudaMemcpyDeviceToHost, s));
+      WCC_CUDA(cudaStreamSynchronize(s));
+    }
+  });
+}
+
+int wcc_number_by_minima(const int32_t *minima, int64_t n, int32_t *labels_out, int64_t *k,
+                         int on_device, void *stream) {
+  return guarded([&] {
+    if (n < 0 || n >= (1ll << 31) - 1) fail(WCC_ERR_INVALID, "n must be in [0, 2^31-1)");
+    if (n > 0 && (minima == nullptr || labels_out == nullptr)) fail(WCC_ERR_INVALID, "NULL buffer");
+    current_device();
+    cudaStream_t s = (cudaStream_t)stream;
+    Workspace ws;
+    DevBuf din, dout;
+    const int32_t *mn = minima;
+    int32_t *o = labels_out;
+    if (!on_device && n > 0) {
+      int32_t *t = static_cast<int32_t *>(din.ensure(4 * n));
+      WCC_CUDA(cudaMemcpyAsync(t, minima, 4 * n, cudaMemcpyHostToDevice, s));
+      mn = t;
+      o = static_cast<int32_t *>(dout.ensure(4 * n));
+    }
+    check_minima(mn, n, ws, s);
+    if (n > 0) number_clusters(mn, n, o, ws, s);
+    int32_t top = -1;
+    if (n > 0) {
+      // ids are dense and ascending by smallest vertex: K = 1 + the largest id
+      int32_t *mx = static_cast<int32_t *>(ws.b[23].ensure(4));
+      WCC_CUDA(cudaMemsetAsync(mx, 0xff, 4, s));
+      k_max_i32_launch(o, n, mx, s);
+      WCC_CUDA(cudaMemcpyAsync(&top, mx, 4, cudaMemcpyDeviceToHost, s));
+    }
+    if (!on_device && n > 0) WCC_CUDA(cudaMemcpyAsync(labels_out, o, 4 * n, cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaStreamSynchronize(s));
+    if (k) *k = (int64_t)top + 1;
   });
 }
 

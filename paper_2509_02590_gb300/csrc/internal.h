@@ -205,6 +205,14 @@ void seed_items(const GroupInfo &gi, int64_t n, Workspace &ws, uint16_t req, Req
 
 // a9: out[v] = rank of the accepted cluster whose smallest vertex is
 // label_min[v] (ascending), -1 where label_min is -1.  Asynchronous on s.
+// Per vertex, the smallest vertex of its cluster (labels in [-1, n)).
+void cluster_minima(const int32_t *labels, int64_t n, int32_t *minima, Workspace &ws,
+                    cudaStream_t s);
+// *out = max(*out, largest entry of a[0..n)).
+void k_max_i32_launch(const int32_t *a, int64_t n, int32_t *out, cudaStream_t s);
+// WCC_ERR_INVALID unless every entry is -1 or a representative r <= v with
+// minima[r] == r.
+void check_minima(const int32_t *minima, int64_t n, Workspace &ws, cudaStream_t s);
 void number_clusters(const int32_t *label_min, int64_t n, int32_t *out, Workspace &ws,
                      cudaStream_t s);
 
@@ -236,6 +244,10 @@ void store_tuning(const wcc_tuning &t);
 bool tuning_valid(const wcc_tuning &t);
 
 wcc_threshold_rule checked_rule(const wcc_threshold_rule *rule);
+// A graph from an edge list, built on the device (the CSR builder of
+// wcc_create_graph_from_edges); host edges are copied first (on_device 0).
+Graph *create_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                         int on_device, cudaStream_t s);
 
 template <typename T>
 T read_back(const T *dev, cudaStream_t s) {

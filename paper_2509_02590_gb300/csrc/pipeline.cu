@@ -294,6 +294,89 @@ void seed_items(const GroupInfo &gi, int64_t n, Workspace &ws, uint16_t req, Req
   WCC_CUDA(cudaGetLastError());
 }
 
+// ---- merging refinements of disjoint sets of input clusters ------------------
+__global__ void k_fill_i32(int32_t *a, int64_t n, int32_t v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+// Per vertex, the smallest vertex of its cluster, from labels in [-1, n):
+// every vertex lowers its label's entry of mins (initially n) to its id.
+__global__ void k_label_mins(const int32_t *__restrict__ lab, int64_t n, int32_t *mins,
+                             unsigned *err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t l = lab[i];
+  if (l < -1 || l >= n) {
+    atomicOr(err, DERR_INVALID);
+    return;
+  }
+  if (l >= 0) atomicMin(&mins[l], (int32_t)i);
+}
+
+__global__ void k_vertex_mins(const int32_t *__restrict__ lab, const int32_t *__restrict__ mins,
+                              int64_t n, int32_t *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t l = lab[i];
+  out[i] = (l >= 0 && l < n) ? mins[l] : -1;
+}
+
+// Minima must name a vertex of the same cluster whose own minimum is
+// itself (a representative), and never exceed the vertex.
+__global__ void k_check_minima(const int32_t *__restrict__ mn, int64_t n, unsigned *err) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t r = mn[i];
+  if (r == -1) return;
+  if (r < 0 || r > i || mn[r] != r) atomicOr(err, DERR_INVALID);
+}
+
+__global__ void k_max_i32(const int32_t *__restrict__ a, int64_t n, int32_t *out) {
+  int32_t m = -1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = a[i] > m ? a[i] : m;
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+void k_max_i32_launch(const int32_t *a, int64_t n, int32_t *out, cudaStream_t s) {
+  const unsigned g = grid_for(n) < 1024u ? grid_for(n) : 1024u;
+  k_max_i32<<<g, TB, 0, s>>>(a, n, out); note_launch();
+  WCC_CUDA(cudaGetLastError());
+}
+
+void cluster_minima(const int32_t *labels, int64_t n, int32_t *minima, Workspace &ws,
+                    cudaStream_t s) {
+  int32_t *mins = buf<int32_t>(ws, B_RANK, n);
+  unsigned *err = buf<unsigned>(ws, B_FLAG, 1);
+  WCC_CUDA(cudaMemsetAsync(err, 0, 4, s));
+  if (n > 0) {
+    k_fill_i32<<<grid_for(n), TB, 0, s>>>(mins, n, (int32_t)n); note_launch();
+    k_label_mins<<<grid_for(n), TB, 0, s>>>(labels, n, mins, err); note_launch();
+    k_vertex_mins<<<grid_for(n), TB, 0, s>>>(labels, mins, n, minima); note_launch();
+    WCC_CUDA(cudaGetLastError());
+  }
+  unsigned h = 0;
+  WCC_CUDA(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaStreamSynchronize(s));
+  if (h) fail(WCC_ERR_INVALID, "a label outside [-1, n)");
+}
+
+void check_minima(const int32_t *minima, int64_t n, Workspace &ws, cudaStream_t s) {
+  unsigned *err = buf<unsigned>(ws, B_TEMP, 1);
+  WCC_CUDA(cudaMemsetAsync(err, 0, 4, s));
+  if (n > 0) {
+    k_check_minima<<<grid_for(n), TB, 0, s>>>(minima, n, err); note_launch();
+    WCC_CUDA(cudaGetLastError());
+  }
+  unsigned h = 0;
+  WCC_CUDA(cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaStreamSynchronize(s));
+  if (h) fail(WCC_ERR_INVALID, "minima: an entry is not the smallest vertex of a cluster");
+}
+
 void number_clusters(const int32_t *label_min, int64_t n, int32_t *out, Workspace &ws,
                      cudaStream_t s) {
   uint32_t *flag = buf<uint32_t>(ws, B_FLAG, n);

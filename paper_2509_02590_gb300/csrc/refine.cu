@@ -88,6 +88,7 @@ struct Mem {
   uint32_t *ebits;     // one bit per local adjacency entry
   IT *adj;
   size_t smem_used;    // bytes of dynamic shared memory the item occupies
+  bool off_in_smem;    // a global-slab item keeps its row offsets in shared memory
 };
 
 template <typename IT>
@@ -118,6 +119,7 @@ __device__ __forceinline__ Mem<IT> carve(char *base, int n, int64_t d) {
   m.adj = (IT *)take(sizeof(IT) * (size_t)d);
   m.vis = reinterpret_cast<uint32_t *>(m.E);
   m.smem_used = 0;
+  m.off_in_smem = false;
   return m;
 }
 
@@ -148,6 +150,7 @@ __device__ __forceinline__ bool carve_hot(Mem<IT> &m, int n, int levels, size_t 
   if (hb + align16(4 * (size_t)(n + 1)) <= smem_bytes) {
     m.off = reinterpret_cast<int32_t *>(h);
     m.smem_used = hb + align16(4 * (size_t)(n + 1));
+    m.off_in_smem = true;
   }
   return true;
 }
@@ -1301,179 +1304,6 @@ __device__ __forceinline__ void ma_pass_bucketed(const Mem<IT> &m, const int32_t
   __syncthreads();
 }
 
-// Exact acceptance test for lambda >= kcap by forest certificates.  Take
-// kcap-1 edge-disjoint spanning forests, each maximal in the edges the earlier
-// ones left.  An edge (u, v) in none of them has u and v joined by a path in
-// every forest (else that forest could have taken it) and by itself: kcap
-// edge-disjoint paths, so lambda(u, v) >= kcap and contracting u, v keeps
-// every cut below kcap (the sparse-certificate argument of Nagamochi and
-// Ibaraki).  Rounds repeat on the contracted multigraph (a super-vertex is
-// labelled by its smallest member; parallel edges stay separate copies).  One
-// super-vertex left certifies lambda >= kcap; that is exactly the item's
-// acceptance, whichever contraction reached it, so the result is the one the
-// canonical passes give.  A super-vertex of degree below kcap (lambda <
-// kcap), a round that contracts nothing, or the round limit gives up and the
-// canonical passes decide.
-//
-// Each forest is grown breadth-first, level-synchronously, from the smallest
-// vertex: every super-vertex of the frontier claims its unclaimed
-// neighbours over unused edges (compare-and-swap on the level).  An
-// unclaimed super-vertex that still has an unused edge starts a further
-// tree.  A tree edge is marked used on both of its adjacency entries (rows
-// are ascending, so the reverse entry is a binary search away).
-// Returns the rounds taken (> 0: certified) or minus the rounds tried.
-// Uses C, D, E, G, H, ebits.
-constexpr int FOREST_MAX_K = 16;       // at most 15 forests a round
-constexpr int FOREST_ROUNDS = 6;
-constexpr int FOREST_EXTRA_TREES = 16; // trees beyond the first per forest
-constexpr int FOREST_LONG_ROW = 32;    // rows longer than this go to a whole warp
-
-template <typename IT>
-__device__ __forceinline__ int find_entry(const Mem<IT> &m, int b, int a) {
-  int lo = m.off[b], hi = m.off[b + 1];
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if ((int)m.adj[mid] < a) lo = mid + 1; else hi = mid;
-  }
-  return lo;  // rows are symmetric, so a is there
-}
-
-// Calls f(a, q, b) for every adjacency entry q = (a -> b) of every alive
-// vertex a with sel(a): rows up to FOREST_LONG_ROW entries by one thread,
-// longer rows (listed in lr[0..nlr)) by a whole warp.
-template <typename IT, typename Sel, typename F>
-__device__ __forceinline__ void rows_pass(const Mem<IT> &m, int n, const int32_t *lr, int nlr,
-                                          Sel sel, F f) {
-  for (int a = threadIdx.x; a < n; a += RB) {
-    if (!m.alive[a]) continue;
-    const int b0 = m.off[a], e0 = m.off[a + 1];
-    if (e0 - b0 > FOREST_LONG_ROW || !sel(a)) continue;
-    for (int q = b0; q < e0; ++q) f(a, q, (int)m.adj[q]);
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = warp; k < nlr; k += RW) {
-    const int a = lr[k];
-    if (!sel(a)) continue;
-    for (int q = m.off[a] + lane; q < m.off[a + 1]; q += 32) f(a, q, (int)m.adj[q]);
-  }
-}
-
-template <typename IT>
-__device__ __forceinline__ int forest_accept(const Mem<IT> &m, int n, int kcap, Sh &sh, bool prof) {
-  long long tc = prof ? clock64() : 0;
-  auto lap = [&](int k) {  // profile: cycles since the last lap into fdbg[k]
-    if (prof) {
-      const long long t = clock64();
-      if (threadIdx.x == 0) sh.fdbg[k] += t - tc;
-      tc = t;
-    }
-  };
-  int32_t *cf = m.C, *lvl = m.D, *lr = m.E, *rep = m.G, *deg = m.H;
-  uint32_t *used = m.ebits;
-  volatile int32_t *vl = lvl;
-  volatile uint32_t *vu = used;
-  const int E = m.off[n];
-  if (threadIdx.x == 0) {
-    sh.i0 = n;
-    sh.ntouched = 0;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += RB) {
-    cf[i] = i;
-    rep[i] = m.alive[i] ? i : -1;
-    if (m.alive[i]) {
-      atomicMin(&sh.i0, i);
-      if (m.off[i + 1] - m.off[i] > FOREST_LONG_ROW) lr[atomicAdd(&sh.ntouched, 1)] = i;
-    }
-  }
-  __syncthreads();
-  const int root = sh.i0, nlr = sh.ntouched;
-  auto all = [](int) { return true; };
-  auto is_used = [&](int q) { return (vu[q >> 5] >> (q & 31)) & 1u; };
-  for (int round = 1; round <= FOREST_ROUNDS; ++round) {
-    if (round > 1) {
-      for (int i = threadIdx.x; i < n; i += RB) deg[i] = 0;
-      __syncthreads();
-      rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
-        const int A = rep[a], B = rep[b];
-        if (B >= 0 && B != A) atomicAdd(&deg[A], 1);
-      });
-      __syncthreads();
-      int low = 0;
-      for (int i = threadIdx.x; i < n; i += RB) low |= rep[i] == i && deg[i] < kcap;
-      if (__syncthreads_or(low)) return -round;
-      lap(4);
-    }
-    for (int q = threadIdx.x; q < (E + 31) / 32; q += RB) used[q] = 0u;
-    for (int f = 1; f < kcap; ++f) {
-      for (int i = threadIdx.x; i < n; i += RB) lvl[i] = i == root ? 0 : -1;
-      int cur = 0;
-      for (int tree = 0;; ++tree) {
-        for (;;) {
-          __syncthreads();
-          int claimed = 0;
-          rows_pass(m, n, lr, nlr, [&](int a) { return vl[rep[a]] == cur; },
-                    [&](int a, int q, int b) {
-                      const int B = rep[b];
-                      if (B < 0 || B == rep[a] || vl[B] != -1 || is_used(q)) return;
-                      if (atomicCAS(&lvl[B], -1, cur + 1) == -1) {
-                        atomicOr(&used[q >> 5], 1u << (q & 31));
-                        const int r = find_entry(m, b, a);
-                        atomicOr(&used[r >> 5], 1u << (r & 31));
-                        claimed = 1;
-                      }
-                    });
-          if (prof && threadIdx.x == 0) sh.fdbg[1] += 1;
-          if (!__syncthreads_or(claimed)) break;
-          ++cur;
-        }
-        lap(0);
-        // the forest is maximal unless an unclaimed super-vertex still has an
-        // unused edge (its other end is unclaimed too: a claimed end would
-        // have claimed it)
-        if (threadIdx.x == 0) sh.i0 = 0x7fffffff;
-        __syncthreads();
-        rows_pass(m, n, lr, nlr, [&](int a) { return vl[rep[a]] == -1; },
-                  [&](int a, int q, int b) {
-                    const int A = rep[a], B = rep[b];
-                    if (B >= 0 && B != A && !is_used(q)) atomicMin(&sh.i0, A);
-                  });
-        __syncthreads();
-        lap(2);
-        const int X = sh.i0;
-        if (X == 0x7fffffff) break;
-        if (prof && threadIdx.x == 0) sh.fdbg[3] += 1;
-        if (tree >= FOREST_EXTRA_TREES) return -round;
-        ++cur;
-        if (threadIdx.x == 0) lvl[X] = cur;
-      }
-    }
-    __syncthreads();
-    int merged = 0;
-    rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
-      if (b < a) return;  // each undirected edge once
-      const int A = rep[a], B = rep[b];
-      if (B < 0 || B == A || is_used(q)) return;
-      merged |= uf_link(cf, A, B);
-    });
-    if (!__syncthreads_or(merged)) return -round;
-    lap(4);
-    int roots = 0;
-    for (int i = threadIdx.x; i < n; i += RB) {
-      const int r = rep[i];
-      if (r >= 0) {
-        const int nr = uf_find(cf, r);
-        rep[i] = nr;
-        roots += nr == i;
-      }
-    }
-    const int nroots = block_sum_int(roots, sh);
-    lap(5);
-    if (nroots == 1) return round;
-  }
-  return -FOREST_ROUNDS;
-}
-
 // ---- few super-vertices: a dense finish ---------------------------------------
 // With at most 32 super-vertices left (indexed in ascending order of their
 // smallest member, so index order is id order), their integer edge weights
@@ -1777,6 +1607,166 @@ __device__ DenseResult dense_finish_w(int32_t *w, int nsv, int kcap, int32_t *du
   return res;
 }
 
+// Exact acceptance test for lambda >= kcap by forest certificates.  Take
+// kcap-1 edge-disjoint spanning forests, each maximal in the edges the earlier
+// ones left.  An edge (u, v) in none of them has u and v joined by a path in
+// every forest (else that forest could have taken it) and by itself: kcap
+// edge-disjoint paths, so lambda(u, v) >= kcap and contracting u, v keeps
+// every cut below kcap (the sparse-certificate argument of Nagamochi and
+// Ibaraki).  Rounds repeat on the contracted multigraph (a super-vertex is
+// labelled by its smallest member; parallel edges stay separate copies).  One
+// super-vertex left certifies lambda >= kcap; that is exactly the item's
+// acceptance, whichever contraction reached it, so the result is the one the
+// canonical passes give.  When few super-vertices are left, the dense
+// finish's capped passes decide on their weight matrix (they keep every cut
+// below kcap as well).  A super-vertex of degree below kcap (lambda < kcap),
+// a round that contracts nothing, too many super-vertices after the last
+// round, or a failing dense check gives up and the canonical passes decide.
+//
+// Each forest is one pass of union-find links over the unused edges (each
+// undirected edge once, from its smaller end): the edges whose link joined
+// two sets form a spanning forest of them, and it is maximal.  The
+// union-find array lives in shared memory when the item leaves room.
+// Returns the rounds taken (> 0: certified) or minus the rounds tried.
+// Uses C, D, E, G, H, ebits (and wide for the dense check).
+constexpr int FOREST_MAX_K = 16;       // at most 15 forests a round
+constexpr int FOREST_ROUNDS = 4;
+constexpr int FOREST_LONG_ROW = 32;    // rows longer than this go to a whole warp
+
+// Calls f(a, q, b) for every adjacency entry q = (a -> b) of every alive
+// vertex a with sel(a): rows up to FOREST_LONG_ROW entries by one thread,
+// longer rows (listed in lr[0..nlr)) by a whole warp.
+template <typename IT, typename Sel, typename F>
+__device__ __forceinline__ void rows_pass(const Mem<IT> &m, int n, const int32_t *lr, int nlr,
+                                          Sel sel, F f) {
+  for (int a = threadIdx.x; a < n; a += RB) {
+    if (!m.alive[a]) continue;
+    const int b0 = m.off[a], e0 = m.off[a + 1];
+    if (e0 - b0 > FOREST_LONG_ROW || !sel(a)) continue;
+    for (int q = b0; q < e0; ++q) f(a, q, (int)m.adj[q]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = warp; k < nlr; k += RW) {
+    const int a = lr[k];
+    if (!sel(a)) continue;
+    for (int q = m.off[a] + lane; q < m.off[a + 1]; q += 32) f(a, q, (int)m.adj[q]);
+  }
+}
+
+template <typename IT>
+__device__ __forceinline__ int forest_accept(const Mem<IT> &m, int n, int kcap, int32_t *cf, Sh &sh,
+                                             bool prof) {
+  long long tc = prof ? clock64() : 0;
+  auto lap = [&](int k) {  // profile: cycles since the last lap into fdbg[k]
+    if (prof) {
+      const long long t = clock64();
+      if (threadIdx.x == 0) sh.fdbg[k] += t - tc;
+      tc = t;
+    }
+  };
+  int32_t *lr = m.D, *rep = m.G, *deg = m.H;
+  uint32_t *used = m.ebits;
+  volatile uint32_t *vu = used;
+  const int E = m.off[n];
+  if (threadIdx.x == 0) sh.ntouched = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += RB) {
+    rep[i] = m.alive[i] ? i : -1;
+    if (m.alive[i] && m.off[i + 1] - m.off[i] > FOREST_LONG_ROW) lr[atomicAdd(&sh.ntouched, 1)] = i;
+  }
+  __syncthreads();
+  const int nlr = sh.ntouched;
+  auto all = [](int) { return true; };
+  auto is_used = [&](int q) { return (vu[q >> 5] >> (q & 31)) & 1u; };
+  int nroots = 0;
+  for (int round = 1; round <= FOREST_ROUNDS; ++round) {
+    if (round > 1) {
+      // a super-vertex with fewer than kcap edges to the others is a cut
+      // below kcap: the item fails, the canonical passes find its cut
+      for (int i = threadIdx.x; i < n; i += RB) deg[i] = 0;
+      __syncthreads();
+      rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
+        const int A = rep[a], B = rep[b];
+        if (B >= 0 && B != A) atomicAdd(&deg[A], 1);
+      });
+      __syncthreads();
+      int low = 0;
+      for (int i = threadIdx.x; i < n; i += RB) low |= rep[i] == i && deg[i] < kcap;
+      if (__syncthreads_or(low)) return -round;
+      lap(4);
+    }
+    for (int q = threadIdx.x; q < (E + 31) / 32; q += RB) used[q] = 0u;
+    for (int f = 1; f < kcap; ++f) {
+      for (int i = threadIdx.x; i < n; i += RB) cf[i] = i;
+      __syncthreads();
+      rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
+        if (b < a) return;  // each undirected edge once
+        const int A = rep[a], B = rep[b];
+        if (B < 0 || B == A || is_used(q)) return;
+        if (uf_link(cf, A, B)) atomicOr(&used[q >> 5], 1u << (q & 31));
+      });
+      __syncthreads();
+      if (prof && threadIdx.x == 0) sh.fdbg[1] += 1;
+      lap(0);
+    }
+    for (int i = threadIdx.x; i < n; i += RB) cf[i] = i;
+    __syncthreads();
+    int merged = 0;
+    rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
+      if (b < a) return;
+      const int A = rep[a], B = rep[b];
+      if (B < 0 || B == A || is_used(q)) return;
+      merged |= uf_link(cf, A, B);
+    });
+    if (!__syncthreads_or(merged)) return -round;
+    lap(2);
+    int roots = 0;
+    for (int i = threadIdx.x; i < n; i += RB) {
+      const int r = rep[i];
+      if (r >= 0) {
+        const int nr = uf_find(cf, r);
+        rep[i] = nr;
+        roots += nr == i;
+      }
+    }
+    nroots = block_sum_int(roots, sh);
+    lap(5);
+    if (nroots == 1) return round;
+    if (nroots <= DENSE_WIDE_NSV && nroots * nroots <= 2 * (n + 1)) {
+      // few super-vertices: the dense finish's capped passes decide
+      int32_t *idx = m.C, *rank = m.H;
+      int32_t *w = reinterpret_cast<int32_t *>(m.wide);
+      for (int i = threadIdx.x; i < n; i += RB) rank[i] = (rep[i] == i) ? 1 : 0;
+      for (int q = threadIdx.x; q < nroots * nroots; q += RB) w[q] = 0;
+      __syncthreads();
+      block_scan_array(rank, n, sh);
+      for (int i = threadIdx.x; i < n; i += RB)
+        if (rep[i] == i) idx[i] = rank[i];
+      __syncthreads();
+      rows_pass(m, n, lr, nlr, all, [&](int a, int q, int b) {
+        const int A = rep[a], B = rep[b];
+        if (B >= 0 && B != A) atomicAdd(&w[idx[A] * nroots + idx[B]], 1);
+      });
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        DenseResult dr;
+        if (nroots <= DENSE_NSV)
+          dr = dense_finish(w, nroots, nroots >= 32 ? 0xffffffffu : (1u << nroots) - 1u, kcap,
+                            sh.duf);
+        else if (nroots <= 64)
+          dr = dense_finish_w<2>(w, nroots, kcap, sh.wduf, sh.wgrp, sh.wside);
+        else
+          dr = dense_finish_w<4>(w, nroots, kcap, sh.wduf, sh.wgrp, sh.wside);
+        if (threadIdx.x == 0) sh.dcut = dr.cut;
+      }
+      __syncthreads();
+      lap(3);
+      return sh.dcut < 0 ? round : -round;
+    }
+  }
+  return -FOREST_ROUNDS;
+}
+
 template <typename IT>
 __device__ __forceinline__ void reset_ma_state(const Mem<IT> &m, int n) {
   for (int i = threadIdx.x; i < n; i += RB) {
@@ -1794,9 +1784,16 @@ __device__ __forceinline__ void reset_ma_state(const Mem<IT> &m, int n) {
 // lane l holds member l's row as a bitmask over local ids, components grow
 // by OR-reductions of rows, the peel is a popcount, and the contraction
 // passes and Stoer-Wagner phases are the dense finish on the same matrix --
-// the same steps and rules as the CTA path, in registers.
+// the same steps and rules as the CTA path, in registers.  The parts an
+// item splits into (components, the two sides of its cut) are subsets of
+// the same matrix, so the warp refines them itself, one after the other,
+// instead of queueing them: each part is the same child item (its vertex
+// set alone decides its outcome, and the local ids keep their order), only
+// without its own claim and extraction.
 constexpr int TINY_MAX = 32;
-constexpr size_t TINY_SCRATCH = 4 * (32 * 32 + 32 + 32);  // weights, union-find, child masks
+// weights, union-find, part stack, row bits, degree prefix
+constexpr size_t TINY_SCRATCH = 4 * (32 * 32 + 32 + 32 + 32 + 32);
+static_assert(TINY_MAX == 32, "one lane per member");
 
 __device__ __forceinline__ uint32_t tiny_component(uint32_t row, uint32_t set, int start) {
   const int l = threadIdx.x & 31;
@@ -1809,62 +1806,16 @@ __device__ __forceinline__ uint32_t tiny_component(uint32_t row, uint32_t set, i
   }
 }
 
-// Queues every mask in cm[0..k) with at least min_size members as a child
-// item, written in place into the parent's pool range (one warp).
-__device__ void tiny_emit(const RefineParams &P, const ReqCtx &R, ReqCtx *Rg, const Item &it,
-                          int32_t v, const uint32_t *cm, int k) {
-  const int l = threadIdx.x & 31;
-  const uint32_t mine = l < k ? cm[l] : 0u;
-  const int size = __popc(mine);
-  const bool keep = l < k && size >= R.min_size;
-  const unsigned kept = __ballot_sync(FULL, keep);
-  const int nchild = __popc(kept);
-  if (nchild == 0) return;
-  const int off = warp_inclusive_scan(keep ? size : 0) - (keep ? size : 0);  // pool offset
-  unsigned long long s0 = 0;
-  if (l == 0) {
-    add_ll(&Rg->pending, (long long)nchild);
-    add_ll(&P.ctr->pending, (long long)nchild);
-    __threadfence();
-    s0 = atomicAdd(&P.ctr->tail, (unsigned long long)nchild);
-  }
-  s0 = __shfl_sync(FULL, s0, 0);
-  // member lanes: the kept child holding them
-  int c = -1;
-  for (int x = 0; x < k; ++x)
-    if (((kept >> x) & 1u) && ((cm[x] >> l) & 1u)) c = x;
-  const int coff = __shfl_sync(FULL, off, c < 0 ? 0 : c);
-  if (c >= 0) {
-    const int pos = __popc(cm[c] & ((1u << l) - 1u));
-    const unsigned long long q = s0 + __popc(kept & ((1u << c) - 1u));
-    R.pool[it.vbeg + coff + pos] = v;
-    R.slot[v] = ((unsigned long long)queue_tag(q) << 32) | (unsigned)pos;
-  }
-  __threadfence();
-  __syncwarp();
-  if (keep) {
-    const unsigned long long q = s0 + __popc(kept & ((1u << l) - 1u));
-    QSlot *sl = &P.ring[q % P.ring_cap];
-    sl->item.vbeg = it.vbeg + off;
-    sl->item.n = size;
-    sl->item.flags = 0;
-    sl->item.req = it.req;
-  }
-  __threadfence();
-  __syncwarp();
-  if (keep) {
-    const unsigned long long q = s0 + __popc(kept & ((1u << l) - 1u));
-    atomicExch((unsigned long long *)&P.ring[q % P.ring_cap].seq, q);
-  }
-}
-
-// Splits a set into its components (masks into cm); returns their count.
-__device__ __forceinline__ int tiny_components(uint32_t row, uint32_t set, uint32_t *cm) {
+// Pushes every component of set (with at least min_size members) onto the
+// part stack stk[0..*sp).  Returns the number of components.
+__device__ __forceinline__ int tiny_push_components(uint32_t row, uint32_t set, int min_size,
+                                                    uint32_t *stk, int &sp) {
   int k = 0;
   uint32_t rem = set;
   while (rem) {
     const uint32_t c = tiny_component(row, set, __ffs(rem) - 1);
-    if ((threadIdx.x & 31) == 0) cm[k] = c;
+    if ((threadIdx.x & 31) == 0 && __popc(c) >= min_size) stk[sp] = c;
+    sp += __popc(c) >= min_size ? 1 : 0;
     ++k;
     rem &= ~c;
   }
@@ -1881,106 +1832,138 @@ __device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, co
   ReqCtx *Rg = &P.reqs[it.req];
   const ReqCtx R = load_ctx(Rg);
   int32_t *w = scratch, *duf = scratch + 32 * 32;
-  uint32_t *cm = reinterpret_cast<uint32_t *>(scratch + 32 * 32 + 32);
+  uint32_t *stk = reinterpret_cast<uint32_t *>(scratch + 32 * 32 + 32);
+  uint32_t *rbits = reinterpret_cast<uint32_t *>(scratch + 32 * 32 + 64);
+  int32_t *pre = scratch + 32 * 32 + 96;
   const bool mine = l < n;
   const int32_t v = mine ? __ldcg(&R.pool[it.vbeg + l]) : -1;
   const int64_t rb = mine ? R.off[v] : 0, re = mine ? R.off[v + 1] : 0;
   const uint32_t tag = queue_tag(seq);
   const int len = (int)(re - rb);
-  const long long D = warp_sum((long long)(mine ? len : 0));
+  const int inc = warp_inclusive_scan(mine ? len : 0);
+  const int D = __shfl_sync(FULL, inc, 31);
   if (D > P.tiny_max_deg) return false;
-  // 1. extraction: rows of up to 64 entries by their own lane, four entries
-  // at a time; longer rows by the whole warp, one after the other
-  const bool shortrow = len <= 64;
-  uint32_t row = 0u;
-  const int wl = warp_max(shortrow ? len : 0);
-  for (int k = 0; k < wl; k += 4) {
-    int32_t u[4];
-    unsigned long long sl[4];
+  // 1. extraction, flat over the D adjacency entries of the members: lane l
+  // takes entries l, l+32, ..., eight at a time (eight neighbour loads, then
+  // eight slot gathers in flight); entry f belongs to the row whose degree
+  // prefix first exceeds f, and a hit sets that row's bit in shared memory
+  pre[l] = inc;
+  rbits[l] = 0u;
+  __syncwarp();
+  constexpr int Q = 8;
+  for (int f0 = 0; f0 < D; f0 += 32 * Q) {
+    int32_t u[Q];
+    int rr[Q];
 #pragma unroll
-    for (int z = 0; z < 4; ++z) u[z] = (shortrow && k + z < len) ? R.adj[rb + k + z] : -1;
-#pragma unroll
-    for (int z = 0; z < 4; ++z) sl[z] = u[z] >= 0 ? __ldcg(&R.slot[u[z]]) : 0ull;
-#pragma unroll
-    for (int z = 0; z < 4; ++z)
-      if (u[z] >= 0 && (unsigned)(sl[z] >> 32) == tag) row |= 1u << (sl[z] & 31u);
-  }
-  unsigned longs = __ballot_sync(FULL, mine && !shortrow);
-  while (longs) {
-    const int src = __ffs(longs) - 1;
-    longs &= longs - 1;
-    const int64_t b = __shfl_sync(FULL, rb, src), e = __shfl_sync(FULL, re, src);
-    uint32_t acc = 0u;
-    for (int64_t q = b + l; q < e; q += 32) {
-      const unsigned long long sl = __ldcg(&R.slot[R.adj[q]]);
-      if ((unsigned)(sl >> 32) == tag) acc |= 1u << (sl & 31u);
+    for (int z = 0; z < Q; ++z) {
+      const int f = f0 + 32 * z + l;
+      int lo = 0, hi = 31;  // smallest r with pre[r] > f
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] > f) hi = mid; else lo = mid + 1;
+      }
+      rr[z] = f < D ? lo : -1;
     }
-    acc = __reduce_or_sync(FULL, acc);
-    if (l == src) row |= acc;
+#pragma unroll
+    for (int z = 0; z < Q; ++z) {
+      const int r = rr[z] < 0 ? 0 : rr[z];
+      const int64_t br = __shfl_sync(FULL, rb, r);
+      const int sr = pre[r] - __shfl_sync(FULL, len, r);
+      u[z] = rr[z] >= 0 ? R.adj[br + (f0 + 32 * z + l - sr)] : -1;
+    }
+    unsigned long long sl[Q];
+#pragma unroll
+    for (int z = 0; z < Q; ++z) sl[z] = u[z] >= 0 ? __ldcg(&R.slot[u[z]]) : 0ull;
+#pragma unroll
+    for (int z = 0; z < Q; ++z)
+      if (u[z] >= 0 && (unsigned)(sl[z] >> 32) == tag) atomicOr(&rbits[rr[z]], 1u << (sl[z] & 31u));
   }
-  if (l == 0) {
-    add_ll(&Rg->items, 1ll);
-    add_ll(&Rg->alg_bytes, ((it.flags & ITEM_TOP) ? 8ll * n : 0ll) + 8ll * D);
-  }
+  __syncwarp();
+  const uint32_t row = mine ? rbits[l] : 0u;
+  // statistics of the whole subtree, added once at the end (lane 0)
+  long long st_items = 1, st_peeled = 0, st_passes = 0, st_phases = 0, st_acc = 0, st_splits = 0;
+  bool failed = false;
   const uint32_t all = n >= 32 ? 0xffffffffu : (1u << n) - 1u;
-  // 2. input cluster: CCR (Algorithm 1)
+  int sp = 0;
+  bool whole = true;  // the item itself is refined as it is
+  // 2. input cluster: CCR (Algorithm 1); when it splits, its components are
+  // the parts
   if (it.flags & ITEM_TOP) {
-    const int k = tiny_components(row, all, cm);
-    if (k != 1) {
-      tiny_emit(P, R, Rg, it, v, cm, k);
-      return true;
-    }
+    const int k = tiny_push_components(row, all, R.min_size, stk, sp);
+    if (k == 1) sp = 0;
+    else whole = false;
   }
-  // 3. peel, round-synchronous, T from the alive count
-  uint32_t cur = all;
+  uint32_t set = all;
   for (;;) {
-    const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, __popc(cur));
-    const unsigned rm = __ballot_sync(FULL, ((cur >> l) & 1u) && __popc(row & cur) <= T);
-    if (!rm) break;
-    cur &= ~rm;
-  }
-  const int nal = __popc(cur);
-  if (nal < n && l == 0) add_ll(&Rg->peeled, (long long)(n - nal));
-  if (nal < R.min_size) return true;
-  // 4. connectivity of what is left (only a peel can disconnect it)
-  if (nal < n) {
-    const int k = tiny_components(row, cur, cm);
-    if (k > 1) {
-      tiny_emit(P, R, Rg, it, v, cm, k);
-      return true;
+    if (!whole) {
+      if (sp == 0) break;
+      set = stk[--sp];
+      st_items += 1;
     }
-  }
-  // 5-6. contraction with k = T+1, then canonical Stoer-Wagner: the dense
-  // finish on the item's own vertices (index = local id)
-  const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, nal);
-  const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
-  const uint32_t rw = ((cur >> l) & 1u) ? row & cur : 0u;
+    whole = false;
+    __syncwarp();
+    const int nset = __popc(set);
+    // 3. peel, round-synchronous, T from the alive count
+    uint32_t cur = set;
+    for (;;) {
+      const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, __popc(cur));
+      const unsigned rm = __ballot_sync(FULL, ((cur >> l) & 1u) && __popc(row & cur) <= T);
+      if (!rm) break;
+      cur &= ~rm;
+    }
+    const int nal = __popc(cur);
+    st_peeled += nset - nal;
+    if (nal < R.min_size) continue;
+    // 4. connectivity of what is left (only a peel can disconnect it)
+    if (nal < nset) {
+      const int sp0 = sp;
+      const int k = tiny_push_components(row, cur, R.min_size, stk, sp);
+      if (k > 1) continue;
+      sp = sp0;  // one component: refine it as it is
+    }
+    // 5-6. contraction with k = T+1, then canonical Stoer-Wagner: the dense
+    // finish on the part's own vertices (index = local id)
+    const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, nal);
+    const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
+    const uint32_t rw = ((cur >> l) & 1u) ? row & cur : 0u;
 #pragma unroll 8
-  for (int b = 0; b < 32; ++b) w[l * 32 + b] = (int32_t)((rw >> b) & 1u);
-  __syncwarp();
-  const DenseResult dr = dense_finish(w, 32, cur, kcap, duf);
+    for (int b = 0; b < 32; ++b) w[l * 32 + b] = (int32_t)((rw >> b) & 1u);
+    __syncwarp();
+    const DenseResult dr = dense_finish(w, 32, cur, kcap, duf);
+    st_passes += dr.passes;
+    st_phases += dr.phases;
+    if (dr.cut < 0) {
+      // accept (Algorithm 3: save V_c); output id resolved after the run
+      const int32_t minv = __shfl_sync(FULL, v, __ffs(cur) - 1);
+      if ((cur >> l) & 1u) R.label_min[v] = minv;
+      st_acc += 1;
+      continue;
+    }
+    if (dr.cut > T) {
+      failed = true;
+      break;
+    }
+    // Algorithm 3: bisect on the minimum cut; both sides are parts
+    st_splits += 1;
+    const uint32_t s0 = cur & ~dr.side, s1 = cur & dr.side;
+    if (l == 0) {
+      int q = sp;
+      if (__popc(s0) >= R.min_size) stk[q++] = s0;
+      if (__popc(s1) >= R.min_size) stk[q++] = s1;
+    }
+    sp += (__popc(s0) >= R.min_size ? 1 : 0) + (__popc(s1) >= R.min_size ? 1 : 0);
+    __syncwarp();
+  }
   if (l == 0) {
-    add_ll(&Rg->ni_passes, (long long)dr.passes);
-    add_ll(&Rg->sw_phases, (long long)dr.phases);
+    if (failed) atomicOr(&P.ctr->error, DERR_INTERNAL);
+    add_ll(&Rg->items, st_items);
+    add_ll(&Rg->alg_bytes, ((it.flags & ITEM_TOP) ? 8ll * n : 0ll) + 8ll * D);
+    if (st_peeled) add_ll(&Rg->peeled, st_peeled);
+    if (st_passes) add_ll(&Rg->ni_passes, st_passes);
+    if (st_phases) add_ll(&Rg->sw_phases, st_phases);
+    if (st_acc) add_ll(&Rg->accepted, st_acc);
+    if (st_splits) add_ll(&Rg->splits, st_splits);
   }
-  if (dr.cut < 0) {
-    // accept (Algorithm 3: save V_c); output id resolved after the run
-    const int32_t minv = __shfl_sync(FULL, v, __ffs(cur) - 1);
-    if ((cur >> l) & 1u) R.label_min[v] = minv;
-    if (l == 0) add_ll(&Rg->accepted, 1ll);
-    return true;
-  }
-  if (dr.cut > T) {
-    if (l == 0) atomicOr(&P.ctr->error, DERR_INTERNAL);
-    return true;
-  }
-  if (l == 0) {
-    add_ll(&Rg->splits, 1ll);
-    cm[0] = cur & ~dr.side;
-    cm[1] = cur & dr.side;
-  }
-  __syncwarp();
-  tiny_emit(P, R, Rg, it, v, cm, 2);
   return true;
 }
 
@@ -2265,7 +2248,13 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   bool inh_valid = false;  // R.inh holds this item's first-pass records
   if (kcap <= FOREST_MAX_K && P.forest_min_n > 0 && nalive >= P.forest_min_n) {
     const long long f0 = P.prof ? clock64() : 0;
-    const int fr = forest_accept(m, n, kcap, sh, P.prof != nullptr);
+    // the forests' union-find: in shared memory for an item in the global
+    // slab when its row offsets did not move there (the first pass's state
+    // there is set up only later)
+    int32_t *cf = m.B;
+    if (!SM && !m.off_in_smem && 4 * (size_t)n <= P.smem_bytes)
+      cf = reinterpret_cast<int32_t *>(wcc_dyn_smem);
+    const int fr = forest_accept(m, n, kcap, cf, sh, P.prof != nullptr);
     certified = fr > 0;
     if (P.prof && threadIdx.x == 0) {
       sh.pf_forest = fr;

@@ -32,7 +32,7 @@ namespace wccg {
 
 namespace {
 
-constexpr int MAX_SLOTS = 64;         // requests refined at the same time
+constexpr int MAX_SLOTS = 256;        // requests refined at the same time
 constexpr int RESERVED_SMS = 8;       // left free for grouping / seeding / numbering
 constexpr uint64_t IDLE_LIMIT_NS = 5ull * 1000 * 1000;
 
@@ -44,6 +44,13 @@ struct Request {
   int64_t n = 0;
   int32_t *h_in = nullptr;   // pinned copy of the input labels
   int32_t *h_out = nullptr;  // pinned result
+  // a request that brings its graph as an edge list: pinned copies of the
+  // edges until admission, then the graph the server builds and owns
+  int32_t *h_src = nullptr, *h_dst = nullptr;
+  int64_t m = 0;
+  std::unique_ptr<Graph> own;
+  size_t build_bytes = 0;    // transient device memory of building that graph
+  bool waited_budget = false;
   wcc_threshold_rule rule{};
   int min_size = 2;
   size_t est_bytes = 0;
@@ -60,6 +67,12 @@ struct Request {
   ~Request() {
     if (h_in) cudaFreeHost(h_in);
     if (h_out) cudaFreeHost(h_out);
+    free_edges();
+  }
+  void free_edges() {
+    if (h_src) cudaFreeHost(h_src);
+    if (h_dst) cudaFreeHost(h_dst);
+    h_src = h_dst = nullptr;
   }
   void release_device() {
     for (auto &b : ws.b) b.release();
@@ -69,6 +82,10 @@ struct Request {
     vslot.release();
     lmin.release();
     inh.release();
+    if (own) {
+      own.reset();
+      g = nullptr;
+    }
   }
 };
 
@@ -77,6 +94,17 @@ struct Request {
 // and the grouping workspace, about 120 bytes per vertex, doubled for the
 // power-of-two block rounding of the allocator, plus 1 MB.
 size_t estimate_bytes(int64_t n) { return (size_t)n * 240 + (1u << 20); }
+
+// A graph the server builds from an edge list: its CSR (int64 offsets,
+// int32 columns for both directions), rounded up like every block, held
+// until the request finishes.
+size_t graph_bytes(int64_t n, int64_t m) { return 2 * (8 * (size_t)(n + 1) + 8 * (size_t)m); }
+
+// The builder's transient memory while one such graph is built (the edge
+// copies, two 64-bit key arrays and two 32-bit flag arrays over the 2m
+// directed entries, scan and sort temporaries), rounded up: needed only
+// during the admission that builds it.
+size_t build_bytes(int64_t n, int64_t m) { return 2 * (56 * (size_t)m + 8 * (size_t)n) + (1u << 20); }
 
 struct Server {
   int device = 0;
@@ -100,6 +128,8 @@ struct Server {
   int n_active = 0;
   bool stop = false;
   uint64_t next_ticket = 1;
+  // counters (wcc_server_info)
+  int64_t admitted = 0, budget_waits = 0, slot_waits = 0, peak_used = 0, peak_active = 0;
 };
 
 void finish(Server *S, Request *R, int status, const std::string &err) {
@@ -113,6 +143,7 @@ void finish(Server *S, Request *R, int status, const std::string &err) {
 
 void free_slot(Server *S, Request *R) {
   if (R->slot >= 0) {
+    std::lock_guard<std::mutex> lk(S->mu);
     S->active[R->slot] = nullptr;
     ((volatile int *)S->done_host)[R->slot] = 0;
     R->slot = -1;
@@ -150,9 +181,16 @@ void finalize(Server *S, Request *R) {
   }
 }
 
-bool can_admit(Server *S, const Request *R) {
-  if (S->n_active >= MAX_SLOTS) return false;
-  if (S->used + (int64_t)R->est_bytes > S->budget) return false;
+bool can_admit(Server *S, Request *R) {
+  if (S->n_active >= MAX_SLOTS) {
+    ++S->slot_waits;
+    return false;
+  }
+  if (S->used + (int64_t)(R->est_bytes + R->build_bytes) > S->budget) {
+    if (!R->waited_budget) ++S->budget_waits;
+    R->waited_budget = true;
+    return false;
+  }
   if ((uint64_t)(S->ring_reserved + R->ring_need) + (uint64_t)S->grid + 1024 > S->ring_cap)
     return false;
   return true;
@@ -164,13 +202,25 @@ void admit(Server *S, Request *R) {
   while (S->active[slot]) ++slot;
   R->slot = slot;
   S->active[slot] = R;
-  ++S->n_active;
-  S->used += (int64_t)R->est_bytes;
-  S->ring_reserved += R->ring_need;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    ++S->n_active;
+    S->used += (int64_t)R->est_bytes;
+    S->ring_reserved += R->ring_need;
+    ++S->admitted;
+    S->peak_used = std::max<int64_t>(S->peak_used, S->used + (int64_t)R->build_bytes);
+    S->peak_active = std::max<int64_t>(S->peak_active, S->n_active);
+  }
   R->t_admit = clock_t_::now();
   try {
     const int64_t n = R->n;
     cudaStream_t s = S->astream;
+    if (R->h_src) {
+      // the request's own graph, built on the device from its edge list
+      R->own.reset(create_from_edges(R->h_src, R->h_dst, R->m, n, 0, s));
+      R->g = R->own.get();
+      R->free_edges();
+    }
     int32_t *d_in = static_cast<int32_t *>(R->d_in.ensure(4 * n));
     WCC_CUDA(cudaMemcpyAsync(d_in, R->h_in, 4 * n, cudaMemcpyHostToDevice, s));
     auto t0 = clock_t_::now();
@@ -371,21 +421,33 @@ void destroy_server(Server *S) {
   delete S;
 }
 
-uint64_t submit(Server *S, Graph *g, const int32_t *labels, const wcc_threshold_rule *rule,
-                int32_t min_size) {
-  if (!g) fail(WCC_ERR_INVALID, "graph is NULL");
-  if (g->device != S->device) fail(WCC_ERR_INVALID, "graph and server are on different devices");
-  if (!labels && g->n > 0) fail(WCC_ERR_INVALID, "clustering_in is NULL");
+// Queues a request: of graph g, or (g == NULL) of the graph of the edge list
+// src[m], dst[m] on n vertices, which the server builds when it admits the
+// request and releases when the request finishes.
+uint64_t submit(Server *S, Graph *g, const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                const int32_t *labels, const wcc_threshold_rule *rule, int32_t min_size) {
   std::unique_ptr<Request> R(new Request());
-  R->g = g;
-  R->n = g->n;
+  if (g) {
+    if (g->device != S->device) fail(WCC_ERR_INVALID, "graph and server are on different devices");
+    n = g->n;
+    R->g = g;
+    R->est_bytes = estimate_bytes(n);
+  } else {
+    if (n < 0 || n >= (1ll << 31) - 1) fail(WCC_ERR_INVALID, "n must be in [0, 2^31-1)");
+    if (m < 0 || 2 * m >= (1ll << 32)) fail(WCC_ERR_INVALID, "m must be in [0, 2^31)");
+    if (m > 0 && (!src || !dst)) fail(WCC_ERR_INVALID, "src/dst is NULL");
+    R->m = m;
+    R->est_bytes = estimate_bytes(n) + graph_bytes(n, m);
+    R->build_bytes = build_bytes(n, m);
+  }
+  if (!labels && n > 0) fail(WCC_ERR_INVALID, "clustering_in is NULL");
+  R->n = n;
   R->rule = checked_rule(rule);
   R->min_size = min_size < 2 ? 2 : min_size;
-  R->est_bytes = estimate_bytes(g->n);
-  R->ring_need = g->n / 2 + 2;
-  if ((int64_t)R->est_bytes > S->budget)
-    fail(WCC_ERR_BUSY, "a graph of " + std::to_string(g->n) +
-                           " vertices needs about " + std::to_string(R->est_bytes) +
+  R->ring_need = n / 2 + 2;
+  if ((int64_t)(R->est_bytes + R->build_bytes) > S->budget)
+    fail(WCC_ERR_BUSY, "a graph of " + std::to_string(n) + " vertices and " + std::to_string(m) +
+                           " edges needs about " + std::to_string(R->est_bytes + R->build_bytes) +
                            " bytes, more than the server's budget");
   if ((uint64_t)R->ring_need + (uint64_t)S->grid + 1024 > S->ring_cap)
     fail(WCC_ERR_BUSY, "the graph is too large for the server's queue");
@@ -394,6 +456,12 @@ uint64_t submit(Server *S, Graph *g, const int32_t *labels, const wcc_threshold_
     WCC_CUDA(cudaHostAlloc((void **)&R->h_in, 4 * R->n, cudaHostAllocDefault));
     WCC_CUDA(cudaHostAlloc((void **)&R->h_out, 4 * R->n, cudaHostAllocDefault));
     std::memcpy(R->h_in, labels, 4 * R->n);
+  }
+  if (!g && m > 0) {
+    WCC_CUDA(cudaHostAlloc((void **)&R->h_src, 4 * m, cudaHostAllocDefault));
+    WCC_CUDA(cudaHostAlloc((void **)&R->h_dst, 4 * m, cudaHostAllocDefault));
+    std::memcpy(R->h_src, src, 4 * m);
+    std::memcpy(R->h_dst, dst, 4 * m);
   }
   std::lock_guard<std::mutex> lk(S->mu);
   const uint64_t t = S->next_ticket++;
@@ -475,8 +543,37 @@ int wcc_submit(wcc_server *s, const wcc_graph *g, const int32_t *clustering_in,
                const wcc_threshold_rule *rule, int32_t min_size, uint64_t *ticket) {
   return guarded_s([&] {
     if (!s || !ticket) fail(WCC_ERR_INVALID, "NULL argument");
-    *ticket = submit(s->s, g ? g->g : nullptr, clustering_in, rule, min_size);
+    if (!g) fail(WCC_ERR_INVALID, "graph is NULL");
+    *ticket = submit(s->s, g->g, nullptr, nullptr, 0, 0, clustering_in, rule, min_size);
     set_last_error("");
+    return (int)WCC_OK;
+  });
+}
+
+int wcc_submit_edges(wcc_server *s, const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                     const int32_t *clustering_in, const wcc_threshold_rule *rule,
+                     int32_t min_size, uint64_t *ticket) {
+  return guarded_s([&] {
+    if (!s || !ticket) fail(WCC_ERR_INVALID, "NULL argument");
+    *ticket = submit(s->s, nullptr, src, dst, m, n, clustering_in, rule, min_size);
+    set_last_error("");
+    return (int)WCC_OK;
+  });
+}
+
+int wcc_server_info(wcc_server *s, wcc_server_counters *out) {
+  return guarded_s([&] {
+    if (!s || !out) fail(WCC_ERR_INVALID, "NULL argument");
+    Server *S = s->s;
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->budget_bytes = S->budget;
+    out->used_bytes = S->used;
+    out->peak_used_bytes = S->peak_used;
+    out->admitted = S->admitted;
+    out->budget_waits = S->budget_waits;
+    out->slot_waits = S->slot_waits;
+    out->peak_active = S->peak_active;
+    out->max_active = MAX_SLOTS;
     return (int)WCC_OK;
   });
 }
