@@ -18,7 +18,8 @@ Workloads (--workload; the default is the one the driver times):
   planted_1k 1,010-vertex planted partition (20 blocks of 50, 4 bridged, 10
              pendant vertices), min size 11; the plain path is its headline;
   dcpp_10m   degree-corrected planted partition, 10M vertices, ~200M edges,
-             power-law cluster sizes 10-50,000, 5% chain clusters;
+             power-law cluster sizes 10-50,000 (exponent 1.8), 5% chain clusters;
+  dcpp_10m_b the same with 500k clusters (size exponent fitted to a mean of 20);
   dcpp_100m  100M vertices, ~2B edges, 5M clusters on [10, 100,000], 3%
              bridged two-part clusters (about 100 GB of device memory).
 The two large ones are generated on the GPU and run with the schedule tuning
@@ -48,8 +49,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "WCC clusters/s and edges/s at 1 GB300 (batched/served vs plain), %HBM roofline; p50/p99"
-WORKLOADS = ("lfr_100k", "planted_1k", "dcpp_10m", "dcpp_100m")
-LARGE = ("dcpp_10m", "dcpp_100m")
+WORKLOADS = ("lfr_100k", "planted_1k", "dcpp_10m", "dcpp_10m_b", "dcpp_100m")
+LARGE = ("dcpp_10m", "dcpp_10m_b", "dcpp_100m")
 
 
 def workload(name: str, rank: int):
@@ -61,6 +62,8 @@ def workload(name: str, rank: int):
     from synth import gpu_graphs
     if name == "dcpp_10m":
         return gpu_graphs.dcpp_10m(seed=rank)
+    if name == "dcpp_10m_b":
+        return gpu_graphs.dcpp_10m_b(seed=rank)
     return gpu_graphs.dcpp_100m(seed=rank)
 
 
@@ -76,6 +79,9 @@ def describe(name: str, w) -> dict:
                       "halves, 10 pendant vertices)",
         "dcpp_10m": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected edges, "
                     f"{n_clusters(w)} clusters (sizes 10-50,000, 5% chains of 2-4 parts)",
+        "dcpp_10m_b": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected "
+                      f"edges, {n_clusters(w)} clusters (sizes 10-50,000 with the exponent fitted "
+                      "to a mean of 20, 5% chains of 2-4 parts)",
         "dcpp_100m": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected edges, "
                      f"{n_clusters(w)} clusters (sizes 10-100,000, 3% bridged two-part clusters)",
     }[name]
@@ -521,74 +527,100 @@ def aggregate_ranks(dist, torch, dev, total_ms: float, m: int, clusters: int):
 
 
 # ------------------------------------------------------------------ serving
-def serving_bench(wcc, np, torch, n_requests: int = 240, pool_size: int = 40, seed: int = 0):
-    """Serving sample of the request-stream workload: a pool of degree-
-    corrected planted-partition graphs with log-uniform edge counts in
-    [1e3, 1e7] (n = m/10, cluster sizes power law 1.5 on [20, 2000], degree
-    exponent 2.5), requests drawn uniformly from the pool.  Capacity is the
-    throughput of a burst of all requests; then the same requests arrive as a
-    Poisson process at 0.5 and at 0.8 of that capacity (0.8 is the headline)
-    and the latency of each (submit to result, wcc_stats.ms_total) is
-    recorded."""
+def serving_bench(wcc, np, torch, n_requests: int = 10_000, pool_size: int = 200, seed: int = 0,
+                  budget: int = 80 << 30, tight_budget: int = 2 << 30, tight_requests: int = 1000):
+    """The request stream: requests whose graphs are degree-corrected planted
+    partitions with log-uniform edge counts in [1e3, 1e7] (n = m/10, cluster
+    sizes power law 1.5 on [20, 2000], degree exponent 2.5), drawn from a
+    pool of distinct seeded graphs held in pinned host memory.  Every
+    request brings its graph as a host edge list (wcc_submit_edges): the
+    server uploads it, builds the CSR, refines, returns the result and frees
+    the graph, all under its memory budget.  Capacity is the throughput of a
+    burst of all requests; then the same requests arrive as a Poisson
+    process at 0.5 and at 0.8 of that capacity (0.8 is the headline) and
+    the latency of each (submit to result, wcc_stats.ms_total) is recorded.
+    A last burst under a tight budget shows the admission control binding."""
     import time as _t
 
     from synth import gpu_graphs
     rng = np.random.default_rng(seed)
     pool = []
+    t_gen = _t.perf_counter()
     for i in range(pool_size):
         m = int(10 ** rng.uniform(3, 7))
         n = max(m // 10, 200)
         w = gpu_graphs.dc_planted_gpu(n, m, seed=1000 + i, deg_exp=2.5, size_exp=1.5,
                                       size_min=20, size_max=2000, f_in=0.8, chain_frac=0.05,
                                       chain_parts=(2, 2))
-        g = wcc.WccGraph.from_edges(w.src, w.dst, w.n)
-        pool.append((g, w.labels.cpu().numpy(), w.m))
+        pool.append((w.src.cpu().pin_memory(), w.dst.cpu().pin_memory(), int(w.n),
+                     w.labels.cpu().numpy(), int(w.m)))
         del w
+    gen_s = _t.perf_counter() - t_gen
     picks = rng.integers(0, pool_size, n_requests)
-    edges = sum(pool[k][2] for k in picks)
+    edges = sum(pool[k][4] for k in picks)
 
-    def stream(rate):
-        """Submit every pick (all at once when rate is None, else Poisson
-        arrivals at rate); returns (seconds, sorted latencies in ms)."""
-        gaps = rng.exponential(1.0 / rate, n_requests) if rate else np.zeros(n_requests)
-        with wcc.WccServer(80 << 30) as srv:
+    def stream(rate, bud, count):
+        """Submit the first count picks (all at once when rate is None, else
+        Poisson arrivals at rate); returns (seconds, sorted latencies in ms,
+        server counters)."""
+        gaps = rng.exponential(1.0 / rate, count) if rate else np.zeros(count)
+        with wcc.WccServer(bud) as srv:
             tickets = []
             t0 = _t.perf_counter()
             nxt = t0
-            for k, gap in zip(picks, gaps):
+            for k, gap in zip(picks[:count], gaps):
                 nxt += gap
                 while _t.perf_counter() < nxt:
                     pass
-                tickets.append(srv.submit(pool[k][0], pool[k][1]))
+                s, d, n, lab, _ = pool[k]
+                tickets.append(srv.submit_edges(s, d, n, lab))
             lat = []
             for t in tickets:
                 _, st = srv.wait(t)
                 lat.append(st["ms_total"])
-            return _t.perf_counter() - t0, sorted(lat)
+            took = _t.perf_counter() - t0
+            info = srv.info()
+        return took, sorted(lat), info
 
     def p(lat, q):
         return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
 
-    burst_s, _ = stream(None)
+    burst_s, _, burst_info = stream(None, budget, n_requests)
     cap_rps = n_requests / burst_s
     loads = {}
     for load in (0.5, 0.8):
-        run_s, lat = stream(load * cap_rps)
+        run_s, lat, info = stream(load * cap_rps, budget, n_requests)
         loads[str(load)] = {"offered_requests_per_s": load * cap_rps,
                             "requests_per_s": n_requests / run_s, "edges_per_s": edges / run_s,
-                            "p50_ms": p(lat, 0.5), "p99_ms": p(lat, 0.99)}
-    for g, _, _ in pool:
-        g.close()
+                            "p50_ms": p(lat, 0.5), "p99_ms": p(lat, 0.99),
+                            "peak_active": info["peak_active"],
+                            "peak_used_bytes": info["peak_used_bytes"]}
+    tight_edges = sum(pool[k][4] for k in picks[:tight_requests])
+    t_s, t_lat, t_info = stream(None, tight_budget, tight_requests)
+    tight = {"budget_bytes": tight_budget, "requests": tight_requests,
+             "requests_per_s": tight_requests / t_s, "edges_per_s": tight_edges / t_s,
+             "p50_ms": p(t_lat, 0.5), "p99_ms": p(t_lat, 0.99),
+             "budget_waits": t_info["budget_waits"], "peak_active": t_info["peak_active"],
+             "peak_used_bytes": t_info["peak_used_bytes"],
+             "budget_left_for_requests": t_info["budget_bytes"]}
     head = loads["0.8"]
     return {"requests": n_requests, "edges": int(edges), "load": 0.8,
             "capacity_requests_per_s": cap_rps, "capacity_edges_per_s": edges / burst_s,
             "requests_per_s": head["requests_per_s"], "edges_per_s": head["edges_per_s"],
             "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "loads": loads,
-            "mean_edges_per_request": edges / n_requests,
-            "sample": f"{n_requests} requests over a pool of {pool_size} graphs "
-                      "(log-uniform 1e3..1e7 edges), 80 GB budget; capacity = a burst of all "
-                      "requests, then Poisson arrivals at 0.5 and 0.8 of it; latency = submit "
-                      "to result"}
+            "burst": {"peak_active": burst_info["peak_active"],
+                      "peak_used_bytes": burst_info["peak_used_bytes"],
+                      "budget_waits": burst_info["budget_waits"],
+                      "slot_waits": burst_info["slot_waits"]},
+            "tight_budget": tight,
+            "mean_edges_per_request": edges / n_requests, "pool_generation_s": gen_s,
+            "sample": f"{n_requests} requests drawn from {pool_size} distinct seeded graphs "
+                      "(log-uniform 1e3..1e7 edges) in pinned host memory; every request "
+                      "uploads its edge list, has its CSR built, refined and freed by the "
+                      f"server under a {budget >> 30} GB budget; capacity = a burst of all "
+                      "requests, then Poisson arrivals at 0.5 and 0.8 of it; latency = "
+                      "submit to result; a burst of the first "
+                      f"{tight_requests} under a {tight_budget >> 30} GB budget"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -603,7 +635,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--resident-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=240)
+    ap.add_argument("--serving-requests", type=int, default=10_000)
+    ap.add_argument("--serving-pool", type=int, default=200)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="run the large configurations with the default tuning")
     ap.add_argument("--no-large-record", action="store_true",
                     help="skip the bounded 10M-vertex record beside the default workload")
     args = ap.parse_args()
@@ -645,7 +680,7 @@ def main():
     # the large configurations run with the schedule's autotuned setting
     # (setup, outside the timed region); the others with the defaults
     tuning = wcc.get_tuning()
-    if large:
+    if large and not args.no_autotune:
         with wcc.WccGraph.from_edges(src_d, dst_d, w.n) as g_t:
             tuning, _ = wcc.autotune(g_t, lab_d, min_size=w.min_size)
 
@@ -778,7 +813,8 @@ def main():
 
     serving = None
     if args.serving_requests > 0 and name == "lfr_100k":
-        serving = serving_bench(wcc, np, torch, n_requests=args.serving_requests, seed=rank)
+        serving = serving_bench(wcc, np, torch, n_requests=args.serving_requests,
+                                pool_size=args.serving_pool, seed=rank)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world,
@@ -787,7 +823,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": describe(name, w),
                 "schedule": {"mode": "batched", "parallelism": f"independent x{world}",
-                             "tuning": tuning | {"autotuned": large}},
+                             "tuning": tuning | {"autotuned": large and not args.no_autotune}},
                 "clusters_per_s": clusters_per_s, "p50_ms": pct(step_ms, 0.5),
                 "p99_ms": pct(step_ms, 0.99),
                 "graph_resident": resident,

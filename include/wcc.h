@@ -173,9 +173,12 @@ int wcc_submit(wcc_server *s, const wcc_graph *g, const int32_t *clustering_in,
 
 /* Queue a refinement of a graph given as an edge list: src[m], dst[m] (host,
  * int32 ids in [0, n)) on n vertices, with clustering_in[n] (host), rule and
- * min_size as in wcc_run.  All three buffers are copied before the call
- * returns.  The server builds the graph on the device when it admits the
- * request (both directions, self-loops and repeated edges dropped, as
+ * min_size as in wcc_run.  clustering_in is copied before the call returns;
+ * src and dst are not: the server reads them when it admits the request, so
+ * they must stay valid and unchanged until the request's result has been
+ * collected (or the server destroyed).  Pinned host memory makes that upload
+ * a direct DMA.  The server builds the graph on the device on admission
+ * (both directions, self-loops and repeated edges dropped, as
  * wcc_create_graph_from_edges) and releases it when the request finishes;
  * the graph's CSR counts against the budget for the request's lifetime, the
  * builder's transient memory during the admission.  An id outside [0, n)
@@ -240,7 +243,7 @@ void wcc_server_destroy(wcc_server *s);
  * WCC_ERR_INVALID.  The array is shared by all calls and keeps the last
  * call's contents (each call clears what it needs), so calls that may
  * overlap on the GPU -- different streams, or several host threads -- race
- * and must be serialised by the caller.  The call reads two values back and
+ * and must be serialised by the caller.  The call reads values back and
  * synchronises `stream` before it returns, so it cannot be recorded into a
  * CUDA graph (stream capture). */
 int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
@@ -258,7 +261,7 @@ int wcc_build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, in
  * WCC_TINY_DEG, WCC_DENSE_NSV, WCC_FOREST_MIN_N and WCC_SMEM_KB, when set,
  * take precedence over it. */
 typedef struct wcc_tuning {
-  int32_t tiny_max;      /* 0..32 (0: no item runs on a single warp) */
+  int32_t tiny_max;      /* 0..64 (0: no item runs on a single warp) */
   int32_t tiny_max_deg;  /* >= 0 */
   int32_t dense_max;     /* 0..128 (0: always the sparse passes) */
   int32_t forest_min_n;  /* >= 0 (0: never) */

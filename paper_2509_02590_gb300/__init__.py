@@ -140,6 +140,7 @@ class WccServer:
     def __init__(self, mem_budget_bytes: int):
         self.handle = wcc_server_create(int(mem_budget_bytes))
         self._n = {}
+        self._keep = {}  # edge lists of requests not collected yet
 
     def submit(self, graph: WccGraph, labels, min_size: int = 2, rule="log10", num: int = 1,
                den: int = 1) -> int:
@@ -153,16 +154,22 @@ class WccServer:
 
     def submit_edges(self, src, dst, n: int, labels, min_size: int = 2, rule="log10",
                      num: int = 1, den: int = 1) -> int:
-        """Queue a request that brings its graph as a host edge list; the
-        server builds the graph on admission and releases it afterwards."""
-        s = np.ascontiguousarray(src, dtype=np.int32)
-        d = np.ascontiguousarray(dst, dtype=np.int32)
+        """Queue a request that brings its graph as a host edge list (numpy
+        arrays or CPU tensors, pinned ones upload fastest); the server builds
+        the graph on admission and releases it afterwards.  The edge arrays
+        are held here until the request is collected."""
+        ps, dev_s, _, ks = _buf(src, np.int32)
+        pd, dev_d, _, kd = _buf(dst, np.int32)
+        if dev_s or dev_d:
+            raise TypeError("submit_edges takes host edge lists")
         lab = np.ascontiguousarray(labels, dtype=np.int32)
-        if len(s) != len(d) or len(lab) != n:
+        m = len(ks)
+        if len(kd) != m or len(lab) != n:
             raise ValueError("src and dst must match; labels must have one entry per vertex")
-        t = _binding.wcc_submit_edges(self.handle, s.ctypes.data, d.ctypes.data, len(s), int(n),
-                                      lab.ctypes.data, rule_struct(rule, num, den), min_size)
+        t = _binding.wcc_submit_edges(self.handle, ps, pd, m, int(n), lab.ctypes.data,
+                                      rule_struct(rule, num, den), min_size)
         self._n[t] = int(n)
+        self._keep[t] = (ks, kd)
         return t
 
     def info(self) -> dict:
@@ -177,10 +184,12 @@ class WccServer:
             r = fn(self.handle, ticket, *args, out.ctypes.data, st)
         except WccError:
             self._n.pop(ticket, None)
+            self._keep.pop(ticket, None)
             raise
         if r != _binding.WCC_OK:
             return None
         self._n.pop(ticket, None)
+        self._keep.pop(ticket, None)
         return out[:n], st.as_dict()
 
     def poll(self, ticket: int):
@@ -195,6 +204,7 @@ class WccServer:
         if self.handle:
             wcc_server_destroy(self.handle)
             self.handle = 0
+        self._keep.clear()
 
     def __enter__(self):
         return self

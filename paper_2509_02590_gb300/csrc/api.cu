@@ -137,7 +137,7 @@ uint64_t wait_limit_ns() {
 // The process-wide tuning (wcc_set_tuning / wcc_autotune / wcc_load_tuning);
 // an environment variable, when set, overrides its field.
 static std::mutex g_tune_mu;
-static wcc_tuning g_tune = {32, 1024, 128, 0, 0, {0, 0, 0}};
+static wcc_tuning g_tune = {64, 4096, 128, 0, 0, {0, 0, 0}};
 
 wcc_tuning current_tuning() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -148,7 +148,7 @@ void store_tuning(const wcc_tuning &t) {
   g_tune = t;
 }
 bool tuning_valid(const wcc_tuning &t) {
-  return t.tiny_max >= 0 && t.tiny_max <= 32 && t.tiny_max_deg >= 0 && t.dense_max >= 0 &&
+  return t.tiny_max >= 0 && t.tiny_max <= 64 && t.tiny_max_deg >= 0 && t.dense_max >= 0 &&
          t.dense_max <= 128 && t.forest_min_n >= 0 && t.smem_kb >= 0 && t.reserved[0] == 0 &&
          t.reserved[1] == 0 && t.reserved[2] == 0;
 }
@@ -172,11 +172,11 @@ int dense_max_config() {
   return (int)(v < 0 ? 0 : v > 128 ? 128 : v);
 }
 
-// Items of at most this many vertices (WCC_TINY_N, at most 32; 0 keeps every
+// Items of at most this many vertices (WCC_TINY_N, at most 64; 0 keeps every
 // item on a whole CTA) are refined one per warp, up to 8 at once per CTA.
 int tiny_max_config() {
   const long long v = env_or("WCC_TINY_N", current_tuning().tiny_max);
-  return (int)(v < 0 ? 0 : v > 32 ? 32 : v);
+  return (int)(v < 0 ? 0 : v > 64 ? 64 : v);
 }
 
 // ... unless their members' degree sum exceeds WCC_TINY_DEG (a hub's row would
@@ -277,15 +277,19 @@ __global__ void k_unique_flags(const uint64_t *__restrict__ keys, int64_t n2, ui
   keep[i] = (k != invalid && (i == 0 || keys[i - 1] != k)) ? 1u : 0u;
 }
 
+// The kept entries in order, and the degree of every row.  Keys are sorted,
+// so a warp's entries mostly share a row: one atomic per row and warp.
 __global__ void k_compact_edges(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ keep,
                                 const uint32_t *__restrict__ pos, int64_t n2, int b,
                                 int32_t *cols, int64_t *deg) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n2 || !keep[i]) return;
-  uint64_t k = keys[i];
-  int64_t u = (int64_t)(k >> b);
-  cols[pos[i]] = (int32_t)(k & ((1ull << b) - 1));
-  atomicAdd((unsigned long long *)&deg[u], 1ull);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool kept = i < n2 && keep[i];
+  const uint64_t k = kept ? keys[i] : 0ull;
+  const unsigned long long u = kept ? (unsigned long long)(k >> b) : ~0ull;
+  if (kept) cols[pos[i]] = (int32_t)(k & ((1ull << b) - 1));
+  const unsigned peers = __match_any_sync(FULL, u);
+  if (kept && (peers & lanemask_lt()) == 0)
+    atomicAdd((unsigned long long *)&deg[u], (unsigned long long)__popc(peers));
 }
 
 // ---------------------------------------------------------------- helpers
@@ -467,6 +471,7 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     if (mode == WCC_MODE_BATCHED) {
       p.slab = static_cast<char *>(rb[R_SLAB].ensure(slab_bytes * (size_t)grid));
       p.single_item = 0;
+      p.tickets = 1;  // nothing is added while the run lasts
       launch_refine(p, grid, true, s);
     } else {
       p.slab = static_cast<char *>(rb[R_SLAB].ensure(slab_bytes));
@@ -595,7 +600,7 @@ Graph *build_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64
     uint64_t *sorted = k1;
     // valid keys are (u << b) | v < 2^(2b) - 1 (u != v); dropped self-loops
     // carry all ones, so sorting on the low 2b bits puts them last
-    if (radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, s)) sorted = k2;
+    if (radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, d_err, s)) sorted = k2;
     k_unique_flags<<<blocks_for(n2), TB, 0, s>>>(sorted, n2, keep, ~0ull); note_launch();
     exclusive_scan_u32(keep, pos, n2, pos + n2, temp, s);
     int32_t *d_adj = static_cast<int32_t *>(g->adj.ensure(4 * n2));
@@ -607,7 +612,8 @@ Graph *build_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64
     WCC_CUDA(cudaMemcpyAsync(&tail[0], d_err, 4, cudaMemcpyDeviceToHost, s));
     WCC_CUDA(cudaMemcpyAsync(&tail[1], pos + n2, 4, cudaMemcpyDeviceToHost, s));
     WCC_CUDA(cudaStreamSynchronize(s));
-    if (tail[0]) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
+    if (tail[0] & DERR_INVALID) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
+    if (tail[0]) fail(WCC_ERR_TIMEOUT, "CSR build: a bounded wait of the sort ran out");
     nnz = tail[1];
   } else {
     g->adj.ensure(4);
@@ -686,7 +692,7 @@ void build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64
     k_edge_keys<<<blocks_for(m), TB, 0, s>>>(src, dst, m, n, b, k1, err); note_launch();
     WCC_CUDA(cudaGetLastError());
     if (read_back(err, s)) fail(WCC_ERR_INVALID, "edge endpoint outside [0, n)");
-    uint64_t *sorted = radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, s) ? k2 : k1;
+    uint64_t *sorted = radix_sort_keys_u64(k1, k2, n2, 2 * b, temp, err, s) ? k2 : k1;
     k_unique_flags<<<blocks_for(n2), TB, 0, s>>>(sorted, n2, keep, ~0ull); note_launch();
     exclusive_scan_u32(keep, pos, n2, pos + n2, temp, s);
     k_compact_edges<<<blocks_for(n2), TB, 0, s>>>(sorted, keep, pos, n2, b, cols, row_off);
@@ -694,6 +700,7 @@ void build_csr_no_alloc(const int32_t *src, const int32_t *dst, int64_t m, int64
     exclusive_scan_i64(row_off, row_off, n + 1, nullptr, temp, s);
     WCC_CUDA(cudaGetLastError());
     nnz = (int64_t)read_back(pos + n2, s);
+    if (read_back(err, s)) fail(WCC_ERR_TIMEOUT, "wcc_build_csr_no_alloc: a bounded wait of the sort ran out");
   }
   WCC_CUDA(cudaStreamSynchronize(s));
   *nnz_out = nnz;
@@ -736,8 +743,8 @@ void autotune_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *ru
       int32_t wcc_tuning::*field;
       std::vector<int32_t> values;
     };
-    const Knob knobs[] = {{&wcc_tuning::tiny_max, {0, 16, 32}},
-                          {&wcc_tuning::tiny_max_deg, {256, 1024, 4096}},
+    const Knob knobs[] = {{&wcc_tuning::tiny_max, {0, 32, 64}},
+                          {&wcc_tuning::tiny_max_deg, {1024, 4096, 16384}},
                           {&wcc_tuning::dense_max, {32, 64, 128}},
                           {&wcc_tuning::smem_kb, {0, 160}},
                           {&wcc_tuning::forest_min_n, {0, 48}}};

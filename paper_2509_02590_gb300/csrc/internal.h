@@ -43,15 +43,17 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
 void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, void *temp,
                         cudaStream_t s);
 
-// Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  Uses
-// keys/vals and keys_alt/vals_alt as ping-pong buffers; returns true when the
-// sorted result ended in the *_alt buffers.  `temp`: radix_temp_bytes(n).
+// Stable LSD radix sort of (key, value) pairs on key bits [0, bits), one
+// kernel per 8-bit digit.  Uses keys/vals and keys_alt/vals_alt as ping-pong
+// buffers; returns true when the sorted result ended in the *_alt buffers.
+// `temp`: radix_temp_bytes(n).  A bounded wait that runs out sets
+// DERR_TIMEOUT in the device word *err (the caller reads it back).
 size_t radix_temp_bytes(int64_t n);
 bool radix_sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                          int64_t n, int bits, void *temp, cudaStream_t s);
+                          int64_t n, int bits, void *temp, unsigned *err, cudaStream_t s);
 // Same for 64-bit keys without values, on key bits [0, bits).
 bool radix_sort_keys_u64(uint64_t *keys, uint64_t *keys_alt, int64_t n, int bits, void *temp,
-                         cudaStream_t s);
+                         unsigned *err, cudaStream_t s);
 
 // Per-request workspace of the pipeline stages: grown on demand, kept
 // between runs; sk/sv remember where group_by_label() left its sort.
@@ -160,6 +162,7 @@ struct RefineParams {
   int tiny_max;               // items of at most this many vertices run one per warp (0 = never)
   int tiny_max_deg;           // ... when their members' degree sum is at most this
   const volatile int *stop_flag;  // optional, host-mapped: when nonzero, CTAs claim nothing more
+  int tickets;                // closed run: claims are tickets (see k_refine)
   int single_item;            // PLAIN mode: process only queue index `single_index`
   unsigned long long single_index;
   ItemProf *prof;             // optional per-item profile (NULL = off)

@@ -447,7 +447,7 @@ Job *job_load(Graph *g, const char *path, cudaStream_t s) {
     h.sw_phases = st[4];
     h.accepted = st[5];
     h.alg_bytes = st[6];
-    h.seed_end = 0;
+    h.seed_end = 0;  // no block claims over the loaded items: one per claim, same results
     WCC_CUDA(cudaMemcpyAsync(j->req.p, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     if (P) {
       k_job_slots<<<(unsigned)P, 256, 0, s>>>(j->ring.as<QSlot>(), j->pool.as<int32_t>(),

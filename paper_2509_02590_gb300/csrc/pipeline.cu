@@ -222,7 +222,8 @@ GroupInfo group_by_label(const int64_t *off, int64_t n, const int32_t *labels, i
   SeedInfo h0 = read_back(info, s);
   if (h0.err) check_device_error(h0.err, "clustering_in");
   uint32_t *sk = keys, *sv = vals;
-  if (radix_sort_pairs_u32(keys, vals, keys2, vals2, n, (int)bitlen_u64(h0.maxkey), temp, s)) {
+  if (radix_sort_pairs_u32(keys, vals, keys2, vals2, n, (int)bitlen_u64(h0.maxkey), temp,
+                           &info->err, s)) {
     sk = keys2;
     sv = vals2;
   }
@@ -250,6 +251,7 @@ GroupInfo group_by_label(const int64_t *off, int64_t n, const int32_t *labels, i
   exclusive_scan_u32(keep, qidx, n, &info->kept, temp, s);
   WCC_CUDA(cudaGetLastError());
   SeedInfo hi = read_back(info, s);
+  if (hi.err) check_device_error(hi.err, "grouping");
   gi.clusters = hi.clusters;
   gi.skip = hi.skip;
   gi.kept = (int64_t)hi.kept;
@@ -265,10 +267,13 @@ GroupInfo group_by_label(const int64_t *off, int64_t n, const int32_t *labels, i
     k_size_keys<<<grid_for(K), TB, 0, s>>>(cstart, keep, K, (uint32_t)gi.max_n, ok1, ov1);
     note_launch();
     uint32_t *ov = ov1;
-    if (radix_sort_pairs_u32(ok1, ov1, ok2, ov2, K, (int)bitlen_u64(gi.max_n + 1), temp, s))
+    if (radix_sort_pairs_u32(ok1, ov1, ok2, ov2, K, (int)bitlen_u64(gi.max_n + 1), temp,
+                             &info->err, s))
       ov = ov2;
     k_invert<<<grid_for(gi.kept), TB, 0, s>>>(ov, gi.kept, qidx); note_launch();
     WCC_CUDA(cudaGetLastError());
+    const unsigned e = read_back(&info->err, s);
+    if (e) check_device_error(e, "grouping");
   }
   return gi;
 }

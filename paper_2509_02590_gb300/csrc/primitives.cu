@@ -1,6 +1,8 @@
 // primitives.cu -- device-wide prefix sums and stable LSD radix sorts used by
 // the membership grouping and the CSR builder.  HBM-bound; tiles of
 // SCAN_BLOCK x SCAN_ITEMS elements.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace wccg {
@@ -101,95 +103,231 @@ void exclusive_scan_impl(const T *in, T *out, int64_t n, T *total, void *temp, c
 }
 
 // ---- radix sort -------------------------------------------------------------
-// One pass = digit histogram per tile, scan of the digit-major histogram
-// table, then a stable scatter.  Stability inside a tile: elements are ranked
-// in index order, with __match_any_sync giving each element its rank among
-// equal digits of its warp and a per-warp count table giving the warps
-// before it.
+// Stable LSD radix sort, 8-bit digits, one kernel per pass ("one sweep"):
+//   - one read of all keys first counts the digits of every pass (a digit's
+//     global count does not depend on the order), and their exclusive
+//     prefix gives each digit's start in the output of every pass;
+//   - in a pass, each CTA takes the next tile (a counter hands tiles out in
+//     order), ranks its keys among equal digits in index order (per warp by
+//     __match_any_sync and a count table, then across warps), publishes its
+//     per-digit counts, and finds the number of keys of each digit in all
+//     earlier tiles by looking back over their published words (decoupled
+//     look-back: a tile that has its inclusive prefix ends the walk); the
+//     tile is then staged in shared memory in sorted order and each digit's
+//     run written out contiguously.
+// A status word holds a state (2 bits: aggregate or inclusive prefix), the
+// pass it belongs to (8 bits) and a count; the status array is cleared once
+// per sort.  Every wait on a predecessor is bounded: past the limit the
+// sort sets DERR_TIMEOUT in *err and leaves its result unspecified.
+
+constexpr int OS_SI = 12;                 // keys per thread
+constexpr int OS_TILE = SB * OS_SI;       // keys per tile
+constexpr int OS_MAXPASS = 8;             // 64-bit keys
+constexpr unsigned long long ST_AGG = 1ull << 62, ST_PRE = 2ull << 62;
+constexpr unsigned long long ST_VAL = (1ull << 54) - 1;
+
+int64_t os_tiles(int64_t n) { return (n + OS_TILE - 1) / OS_TILE; }
 
 template <typename K>
 __device__ __forceinline__ unsigned digit_of(K k, int shift) {
   return (unsigned)((k >> shift) & (K)0xff);
 }
 
+// hist[p][d] += count of keys whose digit p is d (all passes, one read)
 template <typename K>
-__global__ void __launch_bounds__(SB) k_radix_hist(const K *__restrict__ keys, int64_t n,
-                                                  int shift, uint32_t *__restrict__ hist,
-                                                  int64_t nt) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * TILE;
+__global__ void __launch_bounds__(SB) k_digit_counts(const K *__restrict__ keys, int64_t n,
+                                                    int npass, uint32_t *__restrict__ hist) {
+  __shared__ uint32_t h[OS_MAXPASS][256];
 #pragma unroll
-  for (int k = 0; k < SI; k++) {
-    int64_t i = base + (int64_t)k * SB + threadIdx.x;
-    if (i < n) atomicAdd(&h[digit_of(keys[i], shift)], 1u);
+  for (int p = 0; p < OS_MAXPASS; ++p) h[p][threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * SB + threadIdx.x; i < n; i += (int64_t)gridDim.x * SB) {
+    const K k = keys[i];
+    for (int p = 0; p < npass; ++p) atomicAdd(&h[p][digit_of(k, 8 * p)], 1u);
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
+  for (int p = 0; p < npass; ++p)
+    if (h[p][threadIdx.x]) atomicAdd(&hist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
+}
+
+// In place: hist[p][d] -> exclusive prefix over d (one block, thread = digit).
+__global__ void __launch_bounds__(SB) k_digit_starts(uint32_t *hist, int npass) {
+  __shared__ uint32_t sm[SB / 32 + 1];
+  for (int p = 0; p < npass; ++p) {
+    const uint32_t v = hist[p * 256 + threadIdx.x];
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<SB>(v, &tot, sm);
+    hist[p * 256 + threadIdx.x] = ex;
+  }
 }
 
 template <typename K, bool HAS_VAL>
-__global__ void __launch_bounds__(SB) k_radix_scatter(const K *__restrict__ kin,
-                                                     const uint32_t *__restrict__ vin,
-                                                     K *__restrict__ kout,
-                                                     uint32_t *__restrict__ vout, int64_t n,
-                                                     int shift,
-                                                     const uint32_t *__restrict__ offs,
-                                                     int64_t nt) {
+__global__ void __launch_bounds__(SB) k_onesweep(const K *__restrict__ kin,
+                                                const uint32_t *__restrict__ vin,
+                                                K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                int64_t n, int shift, unsigned tag,
+                                                const uint32_t *__restrict__ gbase,
+                                                unsigned long long *status, unsigned *tile_ctr,
+                                                unsigned *err, unsigned long long wait_ns) {
   constexpr int NW = SB / 32;
-  __shared__ uint32_t base_d[256];
-  __shared__ uint32_t wcnt[NW][256];
+  __shared__ uint32_t wcnt[NW][256];  // per-warp digit counts, then per-warp offsets
+  __shared__ uint32_t dstart[256];    // tile-local start of each digit
+  __shared__ unsigned long long gpos[256];  // where each digit's run of this tile goes
+  __shared__ uint32_t scan_sm[NW + 1];
+  __shared__ unsigned tile_sh;
+  __shared__ K stage[OS_TILE];
+  __shared__ uint32_t vstage[HAS_VAL ? OS_TILE : 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  base_d[threadIdx.x] = offs[(int64_t)threadIdx.x * nt + blockIdx.x];
-  const int64_t tbase = (int64_t)blockIdx.x * TILE;
-  for (int k = 0; k < SI; k++) {
-    int64_t i = tbase + (int64_t)k * SB + threadIdx.x;
-    bool valid = i < n;
-    K key = valid ? kin[i] : K(0);
-    uint32_t val = (HAS_VAL && valid) ? vin[i] : 0u;
-    unsigned d = valid ? digit_of(key, shift) : 256u;
-    unsigned peers = __match_any_sync(FULL, d);
-    unsigned rank = __popc(peers & lanemask_lt());
+  if (threadIdx.x == 0) tile_sh = atomicAdd(tile_ctr, 1u);
 #pragma unroll
-    for (int w = 0; w < NW; w++) wcnt[w][threadIdx.x] = 0;
-    __syncthreads();
-    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-    __syncthreads();
-    uint32_t run = 0;
+  for (int w = 0; w < NW; ++w) wcnt[w][threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned tile = tile_sh;
+  const int64_t tbase = (int64_t)tile * OS_TILE;
+  const int tn = (int)min((int64_t)OS_TILE, n - tbase);
+  K key[OS_SI];
+  uint32_t val[OS_SI];
+  uint32_t lrank[OS_SI];
+  unsigned dig[OS_SI];
 #pragma unroll
-    for (int w = 0; w < NW; w++) {
-      uint32_t c = wcnt[w][threadIdx.x];
-      wcnt[w][threadIdx.x] = run;
-      run += c;
-    }
-    __syncthreads();
-    if (valid) {
-      uint32_t pos = base_d[d] + wcnt[warp][d] + rank;
-      kout[pos] = key;
-      if (HAS_VAL) vout[pos] = val;
-    }
-    __syncthreads();
-    base_d[threadIdx.x] += run;
-    (void)lane;
+  for (int k = 0; k < OS_SI; ++k) {
+    const int li = warp * (32 * OS_SI) + k * 32 + lane;  // tile-local index
+    const bool valid = li < tn;
+    key[k] = valid ? kin[tbase + li] : K(0);
+    val[k] = (HAS_VAL && valid) ? vin[tbase + li] : 0u;
+    dig[k] = valid ? digit_of(key[k], shift) : 256u;
   }
+#pragma unroll
+  for (int k = 0; k < OS_SI; ++k) {
+    const unsigned d = dig[k];
+    const unsigned peers = __match_any_sync(FULL, d);
+    const unsigned before = __popc(peers & lanemask_lt());
+    const uint32_t base = d < 256u ? wcnt[warp][d] : 0u;
+    __syncwarp();
+    if (d < 256u && before == 0) wcnt[warp][d] = base + __popc(peers);
+    __syncwarp();
+    lrank[k] = base + before;
+  }
+  __syncthreads();
+  // thread t owns digit t: offsets of each warp within the digit, the tile's
+  // count of the digit, the tile-local starts
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const uint32_t x = wcnt[w][threadIdx.x];
+    wcnt[w][threadIdx.x] = c;
+    c += x;
+  }
+  uint32_t tot;
+  dstart[threadIdx.x] = block_exclusive_scan<SB>(c, &tot, scan_sm);
+  // publish this tile's count of digit t, then add up the earlier tiles'
+  const unsigned long long tg = (unsigned long long)(tag & 0xffu) << 54;
+  unsigned long long *my = status + (size_t)tile * 256 + threadIdx.x;
+  unsigned long long excl = 0;
+  if (tile == 0) {
+    atomicExch(my, ST_PRE | tg | (unsigned long long)c);
+  } else {
+    atomicExch(my, ST_AGG | tg | (unsigned long long)c);
+    // eight predecessors' words are loaded at once per step: the walk passes
+    // aggregates until it meets an inclusive prefix (tile 0 always has one)
+    constexpr int LB = 8;
+    int64_t p = (int64_t)tile - 1;
+    const uint64_t t0 = globaltimer_ns();
+    bool done = false;
+    while (!done) {
+      unsigned long long w[LB];
+#pragma unroll
+      for (int z = 0; z < LB; ++z)
+        w[z] = p - z >= 0 ? *(volatile unsigned long long *)(status + (size_t)(p - z) * 256 +
+                                                             threadIdx.x)
+                          : 0ull;
+      int used = 0;
+#pragma unroll
+      for (int z = 0; z < LB; ++z) {
+        if (done || used < z) continue;  // stopped earlier in this window
+        const unsigned long long x = w[z];
+        if ((x >> 62) == 0 || ((x >> 54) & 0xffull) != (tag & 0xffu)) continue;  // not yet
+        excl += x & ST_VAL;
+        used = z + 1;
+        if ((x >> 62) == 2ull || p - z == 0) done = true;
+      }
+      p -= used;
+      if (done) break;
+      if (used == 0 && globaltimer_ns() - t0 > wait_ns) {  // a predecessor never published
+        atomicOr(err, DERR_TIMEOUT);
+        __threadfence();
+        break;
+      }
+    }
+    // published even after a timeout, so that no successor waits in turn
+    atomicExch(my, ST_PRE | tg | (excl + c));
+  }
+  gpos[threadIdx.x] = (unsigned long long)gbase[threadIdx.x] + excl;
+  __threadfence();
+  // after a timeout anywhere the counts may be wrong: write nothing
+  const bool failed = *(volatile unsigned *)err & DERR_TIMEOUT;
+  if (__syncthreads_or(failed)) return;
+#pragma unroll
+  for (int k = 0; k < OS_SI; ++k) {
+    const unsigned d = dig[k];
+    if (d < 256u) {
+      const uint32_t pos = dstart[d] + wcnt[warp][d] + lrank[k];
+      stage[pos] = key[k];
+      if (HAS_VAL) vstage[pos] = val[k];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < tn; i += SB) {
+    const K kk = stage[i];
+    const unsigned d = digit_of(kk, shift);
+    const unsigned long long op = gpos[d] + (unsigned long long)(i - (int)dstart[d]);
+    if (op >= (unsigned long long)n) continue;  // cannot happen with consistent counts
+    kout[op] = kk;
+    if (HAS_VAL) vout[op] = vstage[i];
+  }
+}
+
+// Layout of the sort's temporary memory: digit starts of every pass, the
+// tile counters of every pass, the status words of every tile.
+struct SortTemp {
+  uint32_t *hist;
+  unsigned *tile_ctr;
+  unsigned long long *status;
+};
+SortTemp sort_temp(void *temp) {
+  SortTemp t;
+  char *p = static_cast<char *>(temp);
+  t.hist = reinterpret_cast<uint32_t *>(p);
+  t.tile_ctr = reinterpret_cast<unsigned *>(p + 4 * 256 * OS_MAXPASS);
+  t.status = reinterpret_cast<unsigned long long *>(p + 4 * 256 * OS_MAXPASS + 256);
+  return t;
 }
 
 template <typename K, bool HAS_VAL>
 bool radix_sort_impl(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, int64_t n,
-                     int bits, void *temp, cudaStream_t s) {
+                     int bits, void *temp, unsigned *err, cudaStream_t s) {
   if (n <= 1 || bits <= 0) return false;
   if (n >= (int64_t)1 << 32) fail(WCC_ERR_INVALID, "radix sort: more than 2^32-1 elements");
-  int64_t nt = ntiles_of(n);
-  uint32_t *hist = static_cast<uint32_t *>(temp);
-  void *scan_tmp = hist + 256 * nt;
+  const int npass = (bits + 7) / 8;
+  if (npass > OS_MAXPASS) fail(WCC_ERR_INTERNAL, "radix sort: key too wide");
+  const int64_t nt = os_tiles(n);
+  SortTemp t = sort_temp(temp);
+  WCC_CUDA(cudaMemsetAsync(t.hist, 0, 4 * 256 * OS_MAXPASS + 256, s));
+  WCC_CUDA(cudaMemsetAsync(t.status, 0, sizeof(unsigned long long) * 256 * (size_t)nt, s));
+  {
+    const int64_t blocks = std::min<int64_t>((n + SB - 1) / SB, 1184);
+    k_digit_counts<K><<<(unsigned)blocks, SB, 0, s>>>(keys, n, npass, t.hist); note_launch();
+    k_digit_starts<<<1, SB, 0, s>>>(t.hist, npass); note_launch();
+  }
+  const unsigned long long wait_ns = 1000ull * 1000 * 1000;  // 1 s
   K *ka = keys, *kb = keys_alt;
   uint32_t *va = vals, *vb = vals_alt;
   bool in_alt = false;
-  for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<K><<<(unsigned)nt, SB, 0, s>>>(ka, n, shift, hist, nt); note_launch();
-    exclusive_scan_impl<uint32_t>(hist, hist, 256 * nt, nullptr, scan_tmp, s);
-    k_radix_scatter<K, HAS_VAL><<<(unsigned)nt, SB, 0, s>>>(ka, va, kb, vb, n, shift, hist, nt); note_launch();
+  for (int p = 0; p < npass; ++p) {
+    k_onesweep<K, HAS_VAL><<<(unsigned)nt, SB, 0, s>>>(ka, va, kb, vb, n, 8 * p, (unsigned)(p + 1),
+                                                       t.hist + 256 * p, t.status, t.tile_ctr + p,
+                                                       err, wait_ns);
+    note_launch();
     WCC_CUDA(cudaGetLastError());
     std::swap(ka, kb);
     std::swap(va, vb);
@@ -213,18 +351,17 @@ void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tot
 }
 
 size_t radix_temp_bytes(int64_t n) {
-  int64_t nt = ntiles_of(n);
-  return (size_t)256 * nt * sizeof(uint32_t) + scan_temp_bytes(256 * nt) + 256;
+  return 4 * 256 * OS_MAXPASS + 256 + sizeof(unsigned long long) * 256 * (size_t)os_tiles(n) + 256;
 }
 
 bool radix_sort_pairs_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
-                          int64_t n, int bits, void *temp, cudaStream_t s) {
-  return radix_sort_impl<uint32_t, true>(keys, vals, keys_alt, vals_alt, n, bits, temp, s);
+                          int64_t n, int bits, void *temp, unsigned *err, cudaStream_t s) {
+  return radix_sort_impl<uint32_t, true>(keys, vals, keys_alt, vals_alt, n, bits, temp, err, s);
 }
 
 bool radix_sort_keys_u64(uint64_t *keys, uint64_t *keys_alt, int64_t n, int bits, void *temp,
-                         cudaStream_t s) {
-  return radix_sort_impl<uint64_t, false>(keys, nullptr, keys_alt, nullptr, n, bits, temp, s);
+                         unsigned *err, cudaStream_t s) {
+  return radix_sort_impl<uint64_t, false>(keys, nullptr, keys_alt, nullptr, n, bits, temp, err, s);
 }
 
 }  // namespace wccg

@@ -173,9 +173,11 @@ struct Sh {
   long long pf_forest_cycles, pf_t0;
   long long fdbg[6];
   uint32_t sink[32];  // per-lane dummy targets of branch-free warp code
-  Item batch[RW];     // claimed items: the first one, then more when it is tiny
+  Item batch[RW];     // claimed items: the first one, then more when it is small
   unsigned long long bseq[RW];
   int32_t nb;
+  unsigned long long claim_h;  // first index of the block claimed after the first item
+  int32_t claim_k;             // its length
   int32_t duf[32];    // dense finish: merges of one pass (union-find over indices)
   uint32_t dside;     // dense finish: side of the minimum cut (mask of indices)
   int32_t wduf[128], wgrp[128];  // wide dense finish: union-find, sets of initial indices
@@ -1546,17 +1548,21 @@ __device__ __forceinline__ void dense_order_w(const int32_t *w, int nsv, const u
   merged = __any_sync(FULL, merged);
 }
 
-// Every index 0..nsv-1 starts live.  duf, grp: nsv ints each; side: K words.
+// The live indices are live0[j] (bit l = index l + 32 j) or, with live0
+// NULL, all of 0..nsv-1; a dead index has zero weights.  duf, grp: nsv ints
+// each; side: K words.
 template <int K>
 __device__ DenseResult dense_finish_w(int32_t *w, int nsv, int kcap, int32_t *duf, int32_t *grp,
-                                      uint32_t *side) {
+                                      uint32_t *side, const uint32_t *live0 = nullptr) {
   const int l = threadIdx.x & 31;
   uint32_t live[K];
-  int nlive = nsv;
+  int nlive = 0;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     const int b = 32 * j;
     live[j] = nsv >= b + 32 ? FULL : (nsv > b ? (1u << (nsv - b)) - 1u : 0u);
+    if (live0) live[j] &= live0[j];
+    nlive += __popc(live[j]);
     if (l + b < nsv) grp[l + b] = l + b;
   }
   __syncwarp();
@@ -1777,29 +1783,60 @@ __device__ __forceinline__ void reset_ma_state(const Mem<IT> &m, int n) {
   __syncthreads();
 }
 
-// ---- items of at most 32 vertices: one warp each ---------------------------------
+// ---- items of at most 64 vertices: one warp each ---------------------------------
 // A CTA that claims such an item claims up to RW-1 more at once and gives
-// every tiny one to a warp of its own (larger ones run on the whole CTA
-// afterwards).  With n <= 32 the induced subgraph is a 32x32 bit matrix:
-// lane l holds member l's row as a bitmask over local ids, components grow
-// by OR-reductions of rows, the peel is a popcount, and the contraction
-// passes and Stoer-Wagner phases are the dense finish on the same matrix --
-// the same steps and rules as the CTA path, in registers.  The parts an
-// item splits into (components, the two sides of its cut) are subsets of
-// the same matrix, so the warp refines them itself, one after the other,
-// instead of queueing them: each part is the same child item (its vertex
-// set alone decides its outcome, and the local ids keep their order), only
-// without its own claim and extraction.
-constexpr int TINY_MAX = 32;
-// weights, union-find, part stack, row bits, degree prefix
-constexpr size_t TINY_SCRATCH = 4 * (32 * 32 + 32 + 32 + 32 + 32);
-static_assert(TINY_MAX == 32, "one lane per member");
+// every small one to a warp of its own (larger ones run on the whole CTA
+// afterwards).  With n <= 32 R (R = 1 or 2 rows per lane) the induced
+// subgraph is a bit matrix: lane l holds the rows of members l and l + 32 as
+// bitmasks over local ids, components grow by OR-reductions of rows, the
+// peel is a popcount, and the contraction passes and Stoer-Wagner phases are
+// the dense finish on the same matrix -- the same steps and rules as the CTA
+// path, in registers.  The parts an item splits into (components, the two
+// sides of its cut) are subsets of the same matrix, so the warp refines
+// them itself, one after the other, instead of queueing them: each part is
+// the same child item (its vertex set alone decides its outcome, and the
+// local ids keep their order), only without its own claim and extraction.
+constexpr int TINY_MAX = 64;
 
-__device__ __forceinline__ uint32_t tiny_component(uint32_t row, uint32_t set, int start) {
+template <int R>
+struct TinyMask;
+template <>
+struct TinyMask<1> { using T = uint32_t; };
+template <>
+struct TinyMask<2> { using T = unsigned long long; };
+
+// Scratch of one warp, in ints: weights (32R)^2, union-find and merged sets
+// (2 x 32R), the part stack (32 masks of R words), row bits (32R masks),
+// the degree prefix (32R) and the cut side (4).
+template <int R>
+__host__ __device__ constexpr size_t tiny_scratch_ints() {
+  return (size_t)(32 * R) * (32 * R) + 2 * (32 * R) + 32 * R + (32 * R) * R + 32 * R + 4;
+}
+constexpr size_t TINY_SCRATCH = 4 * tiny_scratch_ints<2>();     // items of up to 64 vertices
+constexpr size_t TINY_SCRATCH_32 = 4 * tiny_scratch_ints<1>();  // up to 32
+static_assert(TINY_SCRATCH % 8 == 0 && TINY_SCRATCH_32 % 8 == 0, "mask arrays stay aligned");
+
+__device__ __forceinline__ uint32_t warp_or(uint32_t x) { return __reduce_or_sync(FULL, x); }
+__device__ __forceinline__ unsigned long long warp_or(unsigned long long x) {
+  const uint32_t lo = __reduce_or_sync(FULL, (uint32_t)x);
+  const uint32_t hi = __reduce_or_sync(FULL, (uint32_t)(x >> 32));
+  return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ int popc_m(uint32_t x) { return __popc(x); }
+__device__ __forceinline__ int popc_m(unsigned long long x) { return __popcll(x); }
+__device__ __forceinline__ int ffs_m(uint32_t x) { return __ffs(x); }
+__device__ __forceinline__ int ffs_m(unsigned long long x) { return __ffsll((long long)x); }
+
+template <int R, typename M>
+__device__ __forceinline__ M tiny_component(const M (&row)[R], M set, int start) {
   const int l = threadIdx.x & 31;
-  uint32_t V = 1u << start, F = V;
+  M V = (M)1 << start, F = V;
   for (;;) {
-    const uint32_t nx = __reduce_or_sync(FULL, ((F >> l) & 1u) ? row : 0u) & set & ~V;
+    M acc = 0;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if ((F >> (l + 32 * j)) & 1u) acc |= row[j];
+    const M nx = warp_or(acc) & set & ~V;
     if (!nx) return V;
     V |= nx;
     F = nx;
@@ -1808,14 +1845,15 @@ __device__ __forceinline__ uint32_t tiny_component(uint32_t row, uint32_t set, i
 
 // Pushes every component of set (with at least min_size members) onto the
 // part stack stk[0..*sp).  Returns the number of components.
-__device__ __forceinline__ int tiny_push_components(uint32_t row, uint32_t set, int min_size,
-                                                    uint32_t *stk, int &sp) {
+template <int R, typename M>
+__device__ __forceinline__ int tiny_push_components(const M (&row)[R], M set, int min_size, M *stk,
+                                                    int &sp) {
   int k = 0;
-  uint32_t rem = set;
+  M rem = set;
   while (rem) {
-    const uint32_t c = tiny_component(row, set, __ffs(rem) - 1);
-    if ((threadIdx.x & 31) == 0 && __popc(c) >= min_size) stk[sp] = c;
-    sp += __popc(c) >= min_size ? 1 : 0;
+    const M c = tiny_component<R, M>(row, set, ffs_m(rem) - 1);
+    if ((threadIdx.x & 31) == 0 && popc_m(c) >= min_size) stk[sp] = c;
+    sp += popc_m(c) >= min_size ? 1 : 0;
     ++k;
     rem &= ~c;
   }
@@ -1825,30 +1863,45 @@ __device__ __forceinline__ int tiny_push_components(uint32_t row, uint32_t set, 
 
 // Returns false, having done nothing, when the members' degree sum exceeds
 // P.tiny_max_deg (a hub's row would keep one warp busy while its CTA waits).
+template <int R>
 __device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, const Item &it,
                                int32_t *scratch) {
+  using M = typename TinyMask<R>::T;
+  constexpr int NV = 32 * R;  // vertices a warp holds
   const int l = threadIdx.x & 31;
   const int n = it.n;
   ReqCtx *Rg = &P.reqs[it.req];
-  const ReqCtx R = load_ctx(Rg);
-  int32_t *w = scratch, *duf = scratch + 32 * 32;
-  uint32_t *stk = reinterpret_cast<uint32_t *>(scratch + 32 * 32 + 32);
-  uint32_t *rbits = reinterpret_cast<uint32_t *>(scratch + 32 * 32 + 64);
-  int32_t *pre = scratch + 32 * 32 + 96;
-  const bool mine = l < n;
-  const int32_t v = mine ? __ldcg(&R.pool[it.vbeg + l]) : -1;
-  const int64_t rb = mine ? R.off[v] : 0, re = mine ? R.off[v + 1] : 0;
-  const uint32_t tag = queue_tag(seq);
-  const int len = (int)(re - rb);
-  const int inc = warp_inclusive_scan(mine ? len : 0);
-  const int D = __shfl_sync(FULL, inc, 31);
+  const ReqCtx Rc = load_ctx(Rg);
+  int32_t *w = scratch, *duf = scratch + NV * NV, *grp = duf + NV;
+  M *stk = reinterpret_cast<M *>(grp + NV);
+  M *rbits = stk + 32;
+  int32_t *pre = reinterpret_cast<int32_t *>(rbits + NV);
+  uint32_t *wside = reinterpret_cast<uint32_t *>(pre + NV);
+  int32_t v[R];
+  int64_t rb[R];
+  int len[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int i = l + 32 * j;
+    v[j] = i < n ? __ldcg(&Rc.pool[it.vbeg + i]) : -1;
+    rb[j] = i < n ? Rc.off[v[j]] : 0;
+    len[j] = i < n ? (int)(Rc.off[v[j] + 1] - rb[j]) : 0;
+  }
+  int D = 0;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int inc = warp_inclusive_scan(len[j]) + D;
+    pre[l + 32 * j] = inc;
+    D = __shfl_sync(FULL, inc, 31);
+  }
   if (D > P.tiny_max_deg) return false;
+  const uint32_t tag = queue_tag(seq);
   // 1. extraction, flat over the D adjacency entries of the members: lane l
   // takes entries l, l+32, ..., eight at a time (eight neighbour loads, then
   // eight slot gathers in flight); entry f belongs to the row whose degree
   // prefix first exceeds f, and a hit sets that row's bit in shared memory
-  pre[l] = inc;
-  rbits[l] = 0u;
+#pragma unroll
+  for (int j = 0; j < R; ++j) rbits[l + 32 * j] = 0;
   __syncwarp();
   constexpr int Q = 8;
   for (int f0 = 0; f0 < D; f0 += 32 * Q) {
@@ -1857,7 +1910,7 @@ __device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, co
 #pragma unroll
     for (int z = 0; z < Q; ++z) {
       const int f = f0 + 32 * z + l;
-      int lo = 0, hi = 31;  // smallest r with pre[r] > f
+      int lo = 0, hi = NV - 1;  // smallest r with pre[r] > f
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (pre[mid] > f) hi = mid; else lo = mid + 1;
@@ -1867,33 +1920,42 @@ __device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, co
 #pragma unroll
     for (int z = 0; z < Q; ++z) {
       const int r = rr[z] < 0 ? 0 : rr[z];
-      const int64_t br = __shfl_sync(FULL, rb, r);
-      const int sr = pre[r] - __shfl_sync(FULL, len, r);
-      u[z] = rr[z] >= 0 ? R.adj[br + (f0 + 32 * z + l - sr)] : -1;
+      int64_t br = __shfl_sync(FULL, rb[0], r & 31);
+      int lr = __shfl_sync(FULL, len[0], r & 31);
+      if (R == 2) {
+        const int64_t b1 = __shfl_sync(FULL, rb[R - 1], r & 31);
+        const int l1 = __shfl_sync(FULL, len[R - 1], r & 31);
+        if (r >= 32) { br = b1; lr = l1; }
+      }
+      const int sr = pre[r] - lr;
+      u[z] = rr[z] >= 0 ? Rc.adj[br + (f0 + 32 * z + l - sr)] : -1;
     }
     unsigned long long sl[Q];
 #pragma unroll
-    for (int z = 0; z < Q; ++z) sl[z] = u[z] >= 0 ? __ldcg(&R.slot[u[z]]) : 0ull;
+    for (int z = 0; z < Q; ++z) sl[z] = u[z] >= 0 ? __ldcg(&Rc.slot[u[z]]) : 0ull;
 #pragma unroll
     for (int z = 0; z < Q; ++z)
-      if (u[z] >= 0 && (unsigned)(sl[z] >> 32) == tag) atomicOr(&rbits[rr[z]], 1u << (sl[z] & 31u));
+      if (u[z] >= 0 && (unsigned)(sl[z] >> 32) == tag)
+        atomicOr(&rbits[rr[z]], (M)1 << (unsigned)(sl[z] & 0xffffffffu));
   }
   __syncwarp();
-  const uint32_t row = mine ? rbits[l] : 0u;
+  M row[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) row[j] = l + 32 * j < n ? rbits[l + 32 * j] : (M)0;
   // statistics of the whole subtree, added once at the end (lane 0)
   long long st_items = 1, st_peeled = 0, st_passes = 0, st_phases = 0, st_acc = 0, st_splits = 0;
   bool failed = false;
-  const uint32_t all = n >= 32 ? 0xffffffffu : (1u << n) - 1u;
+  const M all = n >= NV ? ~(M)0 : (((M)1 << n) - 1);
   int sp = 0;
   bool whole = true;  // the item itself is refined as it is
   // 2. input cluster: CCR (Algorithm 1); when it splits, its components are
   // the parts
   if (it.flags & ITEM_TOP) {
-    const int k = tiny_push_components(row, all, R.min_size, stk, sp);
+    const int k = tiny_push_components<R, M>(row, all, Rc.min_size, stk, sp);
     if (k == 1) sp = 0;
     else whole = false;
   }
-  uint32_t set = all;
+  M set = all;
   for (;;) {
     if (!whole) {
       if (sp == 0) break;
@@ -1902,40 +1964,66 @@ __device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, co
     }
     whole = false;
     __syncwarp();
-    const int nset = __popc(set);
+    const int nset = popc_m(set);
     // 3. peel, round-synchronous, T from the alive count
-    uint32_t cur = set;
+    M cur = set;
     for (;;) {
-      const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, __popc(cur));
-      const unsigned rm = __ballot_sync(FULL, ((cur >> l) & 1u) && __popc(row & cur) <= T);
+      const int64_t T = threshold_of(Rc.rule_kind, Rc.rule_num, Rc.rule_den, popc_m(cur));
+      M rm = 0;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const bool r = ((cur >> (l + 32 * j)) & 1u) && popc_m(row[j] & cur) <= T;
+        rm |= (M)__ballot_sync(FULL, r) << (32 * j);
+      }
       if (!rm) break;
       cur &= ~rm;
     }
-    const int nal = __popc(cur);
+    const int nal = popc_m(cur);
     st_peeled += nset - nal;
-    if (nal < R.min_size) continue;
+    if (nal < Rc.min_size) continue;
     // 4. connectivity of what is left (only a peel can disconnect it)
     if (nal < nset) {
       const int sp0 = sp;
-      const int k = tiny_push_components(row, cur, R.min_size, stk, sp);
+      const int k = tiny_push_components<R, M>(row, cur, Rc.min_size, stk, sp);
       if (k > 1) continue;
       sp = sp0;  // one component: refine it as it is
     }
     // 5-6. contraction with k = T+1, then canonical Stoer-Wagner: the dense
     // finish on the part's own vertices (index = local id)
-    const int64_t T = threshold_of(R.rule_kind, R.rule_num, R.rule_den, nal);
+    const int64_t T = threshold_of(Rc.rule_kind, Rc.rule_num, Rc.rule_den, nal);
     const int kcap = (int)(T + 1 < (1ll << 30) ? T + 1 : (1ll << 30));
-    const uint32_t rw = ((cur >> l) & 1u) ? row & cur : 0u;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = l + 32 * j;
+      const M rw = ((cur >> i) & 1u) ? row[j] & cur : (M)0;
 #pragma unroll 8
-    for (int b = 0; b < 32; ++b) w[l * 32 + b] = (int32_t)((rw >> b) & 1u);
+      for (int b = 0; b < NV; ++b) w[i * NV + b] = (int32_t)((rw >> b) & 1u);
+    }
     __syncwarp();
-    const DenseResult dr = dense_finish(w, 32, cur, kcap, duf);
+    DenseResult dr;
+    M side;
+    if (R == 1) {
+      dr = dense_finish(w, 32, (uint32_t)cur, kcap, duf);
+      side = (M)dr.side;
+    } else {
+      uint32_t live0[2] = {(uint32_t)cur, (uint32_t)((unsigned long long)cur >> 32)};
+      dr = dense_finish_w<2>(w, NV, kcap, duf, grp, wside, live0);
+      __syncwarp();
+      side = (M)wside[0] | ((M)wside[R - 1] << (32 * (R - 1)));
+    }
     st_passes += dr.passes;
     st_phases += dr.phases;
     if (dr.cut < 0) {
       // accept (Algorithm 3: save V_c); output id resolved after the run
-      const int32_t minv = __shfl_sync(FULL, v, __ffs(cur) - 1);
-      if ((cur >> l) & 1u) R.label_min[v] = minv;
+      const int i0 = ffs_m(cur) - 1;
+      int32_t minv = __shfl_sync(FULL, v[0], i0 & 31);
+      if (R == 2) {
+        const int32_t m1 = __shfl_sync(FULL, v[R - 1], i0 & 31);
+        if (i0 >= 32) minv = m1;
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if ((cur >> (l + 32 * j)) & 1u) Rc.label_min[v[j]] = minv;
       st_acc += 1;
       continue;
     }
@@ -1945,13 +2033,13 @@ __device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, co
     }
     // Algorithm 3: bisect on the minimum cut; both sides are parts
     st_splits += 1;
-    const uint32_t s0 = cur & ~dr.side, s1 = cur & dr.side;
+    const M s0 = cur & ~side, s1 = cur & side;
     if (l == 0) {
       int q = sp;
-      if (__popc(s0) >= R.min_size) stk[q++] = s0;
-      if (__popc(s1) >= R.min_size) stk[q++] = s1;
+      if (popc_m(s0) >= Rc.min_size) stk[q++] = s0;
+      if (popc_m(s1) >= Rc.min_size) stk[q++] = s1;
     }
-    sp += (__popc(s0) >= R.min_size ? 1 : 0) + (__popc(s1) >= R.min_size ? 1 : 0);
+    sp += (popc_m(s0) >= Rc.min_size ? 1 : 0) + (popc_m(s1) >= Rc.min_size ? 1 : 0);
     __syncwarp();
   }
   if (l == 0) {
@@ -1969,11 +2057,17 @@ __device__ bool tiny_item_body(const RefineParams &P, unsigned long long seq, co
 
 // tiny_item_body, recorded in the per-item profile when it is enabled
 // (outcome 100, no phase split).
+__device__ __forceinline__ bool tiny_item_any(const RefineParams &P, unsigned long long seq,
+                                              const Item &it, int32_t *scratch) {
+  return it.n <= 32 ? tiny_item_body<1>(P, seq, it, scratch)
+                    : tiny_item_body<2>(P, seq, it, scratch);
+}
+
 __device__ __forceinline__ bool tiny_item(const RefineParams &P, unsigned long long seq,
                                           const Item &it, int32_t *scratch) {
-  if (!P.prof) return tiny_item_body(P, seq, it, scratch);
+  if (!P.prof) return tiny_item_any(P, seq, it, scratch);
   const long long t0 = (long long)globaltimer_ns();
-  const bool done = tiny_item_body(P, seq, it, scratch);
+  const bool done = tiny_item_any(P, seq, it, scratch);
   __syncwarp();
   if ((threadIdx.x & 31) == 0 && done) {
     const unsigned r = atomicAdd(P.prof_count, 1u);
@@ -2535,6 +2629,36 @@ __device__ int run_item(const RefineParams &P, unsigned long long seq, const Ite
                 : process_item<int32_t, false>(P, seq, it, slab, dsum, sh);
 }
 
+// Waits (bounded) for queue index q to be published and reads its item
+// with two 8-byte loads.  False, with DERR_TIMEOUT set, when the wait runs
+// out or the run has failed meanwhile.
+static_assert(offsetof(Item, vbeg) == 0 && offsetof(Item, n) == 8 && offsetof(Item, flags) == 12 &&
+                  offsetof(Item, req) == 14 && sizeof(Item) == 16,
+              "an item is read as two 8-byte words");
+__device__ __forceinline__ bool fetch_item(const RefineParams &P, unsigned long long q, Item &out) {
+  QSlot *sl = &P.ring[q % P.ring_cap];
+  volatile RunCounters *vctr = P.ctr;
+  const uint64_t t1 = globaltimer_ns();
+  unsigned ns2 = 32;
+  for (;;) {
+    if (*(volatile unsigned long long *)&sl->seq == q) break;
+    if (vctr->error != 0 || globaltimer_ns() - t1 > P.wait_limit_ns) {
+      atomicOr(&P.ctr->error, DERR_TIMEOUT);
+      return false;
+    }
+    __nanosleep(ns2);
+    ns2 = ns2 < 1024 ? ns2 * 2 : ns2;
+  }
+  __threadfence();
+  const volatile unsigned long long *w = reinterpret_cast<const volatile unsigned long long *>(&sl->item);
+  const unsigned long long a = w[0], b = w[1];
+  out.vbeg = (int64_t)a;
+  out.n = (int32_t)(uint32_t)b;
+  out.flags = (uint16_t)(b >> 32);
+  out.req = (uint16_t)(b >> 48);
+  return true;
+}
+
 // ---- the persistent kernel ---------------------------------------------------
 // Thread 0 claims a queue index only when one has been reserved (head <
 // tail), by compare-and-swap, and then waits -- bounded by wait_limit_ns --
@@ -2548,128 +2672,158 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
   char *slab = P.slab + (size_t)blockIdx.x * P.slab_bytes;
   RunCounters *ctr = P.ctr;
   volatile RunCounters *vctr = ctr;
-  const bool tiny_ok = P.tiny_max > 0 && P.smem_bytes >= (size_t)RW * TINY_SCRATCH;
+  // items of up to 64 vertices on single warps when the scratch of eight
+  // warps fits the shared memory, else up to 32, else none
+  int tiny_lim = P.tiny_max;
+  if (tiny_lim > 32 && P.smem_bytes < (size_t)RW * TINY_SCRATCH) tiny_lim = 32;
+  if (tiny_lim > 0 && P.smem_bytes < (size_t)RW * TINY_SCRATCH_32) tiny_lim = 0;
+  const size_t tiny_scr = tiny_lim > 32 ? TINY_SCRATCH : TINY_SCRATCH_32;
+  const bool tiny_ok = tiny_lim > 0;
   bool took = false;  // thread 0: this CTA has claimed an item in this launch
   CtaProf cp{0, 0, 0, 0, 0, 0, 0};  // thread 0, profile only
   long long pc = P.prof ? clock64() : 0;
   for (;;) {
-    if (threadIdx.x == 0) {
-      int go = 0;
-      unsigned long long j = 0;
-      const uint64_t t0 = globaltimer_ns();
-      unsigned ns = 32;
-      for (;;) {
-        if (vctr->error != 0) break;
-        if (P.single_item) {
-          j = P.single_index;
-          go = 1;
-          break;
-        }
-        // a job step whose time is up: leave at this item boundary (the
-        // queue keeps everything not yet claimed).  A CTA takes one item
-        // before it looks, so that every step makes progress.
-        if (P.stop_flag && took && *P.stop_flag) break;
-        const unsigned long long h = vctr->head, t = vctr->tail;
-        if (h < t) {
-          if (atomicCAS(&ctr->head, h, h + 1) == h) {
-            j = h;
-            go = 1;
-            took = true;
-            break;
-          }
-          continue;
-        }
-        if (P.stop_flag && *P.stop_flag) break;
-        // an open (serving) kernel leaves as a whole: the first CTA that
-        // idled out closes it for all, so that work admitted meanwhile never
-        // runs on a few stragglers; the host relaunches it for that work
-        if (vctr->closing) break;
-        const long long pend = vctr->pending;
-        const uint64_t waited = globaltimer_ns() - t0;
-        if (pend <= 0) {
-          if (!vctr->open) break;
-          if (waited > P.idle_limit_ns) {
-            atomicExch(&ctr->closing, 1);
-            break;
-          }
-        } else if (waited > P.wait_limit_ns) {
-          atomicOr(&ctr->error, DERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(ns);
-        ns = ns < 4096 ? ns * 2 : ns;
-      }
-      if (go) {
-        // the claimed index is reserved; wait for its publication
-        QSlot *sl = &P.ring[j % P.ring_cap];
-        const uint64_t t1 = globaltimer_ns();
-        unsigned ns2 = 32;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      if (lane == 0 && P.tickets) {
+        // A closed run (nothing is added from outside while it runs) claims
+        // its first item by ticket: a fetch-and-add on the head never fails,
+        // so the CTAs do not contend on a compare-and-swap.  Ticket j is an
+        // item once it is reserved (j < tail); while it is not, the CTA
+        // waits for it, holding no other work, and leaves once nothing is
+        // pending (no item in flight could reserve it any more: an
+        // unfinished reserved index keeps pending above zero).
+        int go = 0;
+        const unsigned long long j = atomicAdd(&ctr->head, 1ull);
+        const uint64_t t0 = globaltimer_ns();
+        unsigned ns = 32;
         for (;;) {
-          if (*(volatile unsigned long long *)&sl->seq == j) break;
-          if (vctr->error != 0 || globaltimer_ns() - t1 > P.wait_limit_ns) {
-            atomicOr(&ctr->error, DERR_TIMEOUT);
-            go = 0;
+          if (vctr->error != 0) break;
+          if (j < vctr->tail) {
+            go = 1;
             break;
           }
-          __nanosleep(ns2);
-          ns2 = ns2 < 1024 ? ns2 * 2 : ns2;
-        }
-        __threadfence();
-        if (go) {
-          volatile Item *vi = &sl->item;
-          sh.batch[0].vbeg = vi->vbeg;
-          sh.batch[0].n = vi->n;
-          sh.batch[0].flags = vi->flags;
-          sh.batch[0].req = vi->req;
-          sh.bseq[0] = j;
-        }
-      }
-      // a tiny input cluster: claim up to RW-1 more at once, one per warp.
-      // A request's input clusters are queued largest first in one range, so
-      // the ones after a tiny one up to the range's end are tiny too; taking
-      // them as a block costs one compare-and-swap and never holds back a
-      // larger item.
-      int nb = go ? 1 : 0;
-      if (go && tiny_ok && !P.single_item && sh.batch[0].n <= P.tiny_max &&
-          (sh.batch[0].flags & ITEM_TOP) && !(P.stop_flag && *P.stop_flag)) {
-        const unsigned long long send = __ldcg(&P.reqs[sh.batch[0].req].seed_end);
-        for (int tries = 0; nb < RW && tries < 8; ++tries) {
-          if (vctr->error != 0) break;
-          const unsigned long long h = vctr->head, t = vctr->tail;
-          const unsigned long long lim = t < send ? t : send;
-          if (h >= lim) break;
-          const int k = (int)min((unsigned long long)(RW - nb), lim - h);
-          if (atomicCAS(&ctr->head, h, h + k) != h) continue;
-          for (int z = 0; z < k; ++z) {
-            QSlot *sl = &P.ring[(h + z) % P.ring_cap];
-            const uint64_t t1 = globaltimer_ns();
-            unsigned ns2 = 32;
-            bool ok = true;
-            for (;;) {
-              if (*(volatile unsigned long long *)&sl->seq == h + z) break;
-              if (vctr->error != 0 || globaltimer_ns() - t1 > P.wait_limit_ns) {
-                atomicOr(&ctr->error, DERR_TIMEOUT);
-                ok = false;
-                break;
-              }
-              __nanosleep(ns2);
-              ns2 = ns2 < 1024 ? ns2 * 2 : ns2;
-            }
-            if (!ok) break;  // the run is failing; the rest stays unprocessed
-            __threadfence();
-            volatile Item *vi = &sl->item;
-            sh.batch[nb].vbeg = vi->vbeg;
-            sh.batch[nb].n = vi->n;
-            sh.batch[nb].flags = vi->flags;
-            sh.batch[nb].req = vi->req;
-            sh.bseq[nb] = h + z;
-            ++nb;
+          if (vctr->pending <= 0) break;
+          if (globaltimer_ns() - t0 > P.wait_limit_ns) {
+            atomicOr(&ctr->error, DERR_TIMEOUT);
+            break;
           }
-          break;
+          __nanosleep(ns);
+          ns = ns < 4096 ? ns * 2 : ns;
         }
+        if (go && !fetch_item(P, j, sh.batch[0])) go = 0;
+        sh.bseq[0] = j;
+        // a small input cluster: the block after it (see below)
+        int k = 0;
+        unsigned long long hb = 0;
+        if (go && tiny_ok && sh.batch[0].n <= tiny_lim && (sh.batch[0].flags & ITEM_TOP)) {
+          const unsigned long long send = __ldcg(&P.reqs[sh.batch[0].req].seed_end);
+          for (int tries = 0; tries < 4; ++tries) {
+            const unsigned long long h = vctr->head, t = vctr->tail;
+            const unsigned long long lim = t < send ? t : send;
+            if (h >= lim) break;
+            const int kk = (int)min((unsigned long long)(RW - 1), lim - h);
+            if (atomicCAS(&ctr->head, h, h + kk) == h) {
+              k = kk;
+              hb = h;
+              break;
+            }
+          }
+        }
+        sh.claim_h = hb;
+        sh.claim_k = k;
+        sh.go = go;
+      } else if (lane == 0) {
+        int go = 0;
+        unsigned long long j = 0;
+        const uint64_t t0 = globaltimer_ns();
+        unsigned ns = 32;
+        for (;;) {
+          if (vctr->error != 0) break;
+          if (P.single_item) {
+            j = P.single_index;
+            go = 1;
+            break;
+          }
+          // a job step whose time is up: leave at this item boundary (the
+          // queue keeps everything not yet claimed).  A CTA takes one item
+          // before it looks, so that every step makes progress.
+          if (P.stop_flag && took && *P.stop_flag) break;
+          const unsigned long long h = vctr->head, t = vctr->tail;
+          if (h < t) {
+            if (atomicCAS(&ctr->head, h, h + 1) == h) {
+              j = h;
+              go = 1;
+              took = true;
+              break;
+            }
+            continue;
+          }
+          if (P.stop_flag && *P.stop_flag) break;
+          // an open (serving) kernel leaves as a whole: the first CTA that
+          // idled out closes it for all, so that work admitted meanwhile
+          // never runs on a few stragglers; the host relaunches it for that
+          // work
+          if (vctr->closing) break;
+          const long long pend = vctr->pending;
+          const uint64_t waited = globaltimer_ns() - t0;
+          if (pend <= 0) {
+            if (!vctr->open) break;
+            if (waited > P.idle_limit_ns) {
+              atomicExch(&ctr->closing, 1);
+              break;
+            }
+          } else if (waited > P.wait_limit_ns) {
+            atomicOr(&ctr->error, DERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(ns);
+          ns = ns < 4096 ? ns * 2 : ns;
+        }
+        if (go && !fetch_item(P, j, sh.batch[0])) go = 0;
+        sh.bseq[0] = j;
+        // a small input cluster: claim up to RW-1 more at once, one per
+        // warp.  A request's input clusters are queued largest first in one
+        // range, so the ones after a small one up to the range's end are
+        // small too; taking them as a block costs one compare-and-swap and
+        // never holds a larger item back behind them
+        int k = 0;
+        unsigned long long hb = 0;
+        if (go && tiny_ok && !P.single_item && sh.batch[0].n <= tiny_lim &&
+            (sh.batch[0].flags & ITEM_TOP) && !(P.stop_flag && *P.stop_flag)) {
+          const unsigned long long send = __ldcg(&P.reqs[sh.batch[0].req].seed_end);
+          for (int tries = 0; tries < 8; ++tries) {
+            if (vctr->error != 0) break;
+            const unsigned long long h = vctr->head, t = vctr->tail;
+            const unsigned long long lim = t < send ? t : send;
+            if (h >= lim) break;
+            const int kk = (int)min((unsigned long long)(RW - 1), lim - h);
+            if (atomicCAS(&ctr->head, h, h + kk) == h) {
+              k = kk;
+              hb = h;
+              break;
+            }
+          }
+        }
+        sh.claim_h = hb;
+        sh.claim_k = k;
+        sh.go = go;
       }
-      sh.nb = nb;
-      sh.go = go;
+      __syncwarp();
+      // the block's items: waited for and read by lanes 1..k at once
+      const int k = sh.claim_k;
+      bool ok = true;
+      if (lane >= 1 && lane <= k) {
+        const unsigned long long q = sh.claim_h + (unsigned long long)(lane - 1);
+        ok = fetch_item(P, q, sh.batch[lane]);
+        sh.bseq[lane] = q;
+      }
+      const unsigned bad = __ballot_sync(FULL, !ok);
+      if (lane == 0) {
+        // a failed wait has set the error: the items after it stay unprocessed
+        const int fetched = bad ? __ffs(bad) - 2 : k;
+        sh.nb = sh.go ? 1 + fetched : 0;
+      }
     }
     __syncthreads();
     if (P.prof && threadIdx.x == 0) {
@@ -2683,10 +2837,10 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
     __syncthreads();
     if (tiny_ok) {
       const int warp = threadIdx.x >> 5;
-      if (warp < nb && sh.batch[warp].n <= P.tiny_max) {
+      if (warp < nb && sh.batch[warp].n <= tiny_lim) {
         const Item ti = sh.batch[warp];
         const bool done = tiny_item(P, sh.bseq[warp], ti,
-                                    reinterpret_cast<int32_t *>(wcc_dyn_smem + (size_t)warp * TINY_SCRATCH));
+                                    reinterpret_cast<int32_t *>(wcc_dyn_smem + (size_t)warp * tiny_scr));
         __syncwarp();
         if ((threadIdx.x & 31) == 0) {
           if (done) finish_item(P, ti.req);
@@ -2700,13 +2854,13 @@ __global__ void __launch_bounds__(RB, 1) k_refine(RefineParams P) {
         pc = t;
         ++cp.batches;
         for (int k = 0; k < nb; ++k)
-          cp.tiny_items += (sh.batch[k].n <= P.tiny_max && !((sh.ntouched >> k) & 1)) ? 1 : 0;
+          cp.tiny_items += (sh.batch[k].n <= tiny_lim && !((sh.ntouched >> k) & 1)) ? 1 : 0;
       }
     }
     const int cta_mask = sh.ntouched;
     for (int k = 0; k < nb; ++k) {
       const Item it = sh.batch[k];
-      if (tiny_ok && it.n <= P.tiny_max && !((cta_mask >> k) & 1)) continue;
+      if (tiny_ok && it.n <= tiny_lim && !((cta_mask >> k) & 1)) continue;
       const unsigned long long iseq = sh.bseq[k];
       if (P.prof && threadIdx.x == 0) {
         const long long t = clock64();

@@ -44,9 +44,10 @@ struct Request {
   int64_t n = 0;
   int32_t *h_in = nullptr;   // pinned copy of the input labels
   int32_t *h_out = nullptr;  // pinned result
-  // a request that brings its graph as an edge list: pinned copies of the
-  // edges until admission, then the graph the server builds and owns
-  int32_t *h_src = nullptr, *h_dst = nullptr;
+  // a request that brings its graph as an edge list: the caller's edge
+  // buffers (valid until the request is collected), then the graph the
+  // server builds from them on admission and owns
+  const int32_t *h_src = nullptr, *h_dst = nullptr;
   int64_t m = 0;
   std::unique_ptr<Graph> own;
   size_t build_bytes = 0;    // transient device memory of building that graph
@@ -67,12 +68,6 @@ struct Request {
   ~Request() {
     if (h_in) cudaFreeHost(h_in);
     if (h_out) cudaFreeHost(h_out);
-    free_edges();
-  }
-  void free_edges() {
-    if (h_src) cudaFreeHost(h_src);
-    if (h_dst) cudaFreeHost(h_dst);
-    h_src = h_dst = nullptr;
   }
   void release_device() {
     for (auto &b : ws.b) b.release();
@@ -215,11 +210,11 @@ void admit(Server *S, Request *R) {
   try {
     const int64_t n = R->n;
     cudaStream_t s = S->astream;
-    if (R->h_src) {
+    if (!R->g) {
       // the request's own graph, built on the device from its edge list
       R->own.reset(create_from_edges(R->h_src, R->h_dst, R->m, n, 0, s));
       R->g = R->own.get();
-      R->free_edges();
+      R->h_src = R->h_dst = nullptr;
     }
     int32_t *d_in = static_cast<int32_t *>(R->d_in.ensure(4 * n));
     WCC_CUDA(cudaMemcpyAsync(d_in, R->h_in, 4 * n, cudaMemcpyHostToDevice, s));
@@ -457,11 +452,9 @@ uint64_t submit(Server *S, Graph *g, const int32_t *src, const int32_t *dst, int
     WCC_CUDA(cudaHostAlloc((void **)&R->h_out, 4 * R->n, cudaHostAllocDefault));
     std::memcpy(R->h_in, labels, 4 * R->n);
   }
-  if (!g && m > 0) {
-    WCC_CUDA(cudaHostAlloc((void **)&R->h_src, 4 * m, cudaHostAllocDefault));
-    WCC_CUDA(cudaHostAlloc((void **)&R->h_dst, 4 * m, cudaHostAllocDefault));
-    std::memcpy(R->h_src, src, 4 * m);
-    std::memcpy(R->h_dst, dst, 4 * m);
+  if (!g) {
+    R->h_src = src;
+    R->h_dst = dst;
   }
   std::lock_guard<std::mutex> lk(S->mu);
   const uint64_t t = S->next_ticket++;

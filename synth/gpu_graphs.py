@@ -210,3 +210,15 @@ def dcpp_100m(seed: int = 0, device: str = "cuda") -> GpuWorkload:
                           size_exp=None, size_mean=20.0, size_min=10, size_max=100_000,
                           f_in=0.8, chain_frac=0.03, chain_parts=(2, 2), device=device,
                           draw_factor=1.19)
+
+
+def dcpp_10m_b(seed: int = 0, device: str = "cuda") -> GpuWorkload:
+    """The second reading of the 10M-vertex configuration: 500k clusters,
+    the size exponent fitted to a mean of 20 on [10, 50000]; 10M vertices,
+    about 200M undirected edges (Chung-Lu exponent 2.2, mean degree 40), 80%
+    intra edges asked for but capped at density 0.5 inside clusters this
+    small (the rest are drawn between clusters; meta holds the realised
+    split), 5% chain clusters of 2-4 parts."""
+    return dc_planted_gpu(10_000_000, 200_000_000, seed=seed, deg_exp=2.2, size_exp=None,
+                          size_mean=20.0, size_min=10, size_max=50_000, f_in=0.8,
+                          chain_frac=0.05, chain_parts=(2, 4), device=device, draw_factor=1.19)

@@ -117,6 +117,21 @@ def test_dcpp_10m_repeated_runs_identical(dcpp10m):
         assert np.array_equal(out_p.numpy(), ref)
 
 
+def test_dcpp_10m_500k_clusters_sampled_parity():
+    """The second reading of the 10M-vertex configuration: 500k clusters of
+    mean size 20."""
+    wcc = _wcc()
+    from synth import gpu_graphs
+    w = gpu_graphs.dcpp_10m_b(seed=0)
+    assert w.n == 10_000_000 and 180_000_000 < w.m < 220_000_000
+    assert 450_000 < w.meta["clusters"] < 550_000
+    ref, got, ost, st, ns = _sampled_parity(wcc, w, n_largest=3, n_chains=30, n_random=600)
+    assert st["in_clusters"] == w.meta["clusters"]
+    assert np.array_equal(got, ref), f"{int((got != ref).sum())} of {ns} sampled vertices differ"
+    del w
+    torch.cuda.empty_cache()
+
+
 def test_dcpp_100m_sampled_parity():
     """About 100 GB of device memory: the 2B-edge graph, its CSR and the
     refinement's working memory."""

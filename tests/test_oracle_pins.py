@@ -201,6 +201,23 @@ def test_item_cut_hand_traced(case):
         assert rep.tolist() == case["rep"]
 
 
+@pytest.mark.parametrize("case", [c for c in GOLDEN["item_cut"] if "plain_sw_side" in c],
+                         ids=lambda c: c["name"])
+def test_cut_rule_contraction_changes_the_side(case):
+    """Reading R5 runs canonical Stoer-Wagner after the capped contraction;
+    the plain canonical Stoer-Wagner on the uncontracted item (the other
+    reading) can return another minimum cut.  Both sides, hand-traced, have
+    the minimum value; the oracle's item cut is the R5 one."""
+    eu, ev = _clique_graph(case)
+    lam, side = oracle.stoer_wagner(case["n"], eu, ev)
+    assert lam == case["lambda"]
+    assert np.nonzero(side)[0].tolist() == case["plain_sw_side"] != case["side"]
+    for s in (case["side"], case["plain_sw_side"]):
+        mask = np.zeros(case["n"], bool)
+        mask[s] = True
+        assert cut_value(eu, ev, mask) == case["lambda"]
+
+
 def test_item_cut_decision_and_side_brute_force():
     """accept <=> lambda > T; on failure lambda is exact and the side is a
     minimum cut not containing vertex 0; the contraction never splits a cut

@@ -11,7 +11,7 @@ import synth
 
 wcc = pytest.importorskip("paper_2509_02590_gb300")
 
-DEFAULT = {"tiny_max": 32, "tiny_max_deg": 1024, "dense_max": 128, "forest_min_n": 0, "smem_kb": 0}
+DEFAULT = {"tiny_max": 64, "tiny_max_deg": 4096, "dense_max": 128, "forest_min_n": 0, "smem_kb": 0}
 
 
 @pytest.fixture(autouse=True)
@@ -27,7 +27,7 @@ def test_defaults_and_round_trip():
                                      "forest_min_n": 64, "smem_kb": 100}
 
 
-@pytest.mark.parametrize("field,value", [("tiny_max", 33), ("tiny_max", -1), ("dense_max", 129),
+@pytest.mark.parametrize("field,value", [("tiny_max", 65), ("tiny_max", -1), ("dense_max", 129),
                                          ("tiny_max_deg", -5), ("smem_kb", -1),
                                          ("forest_min_n", -2)])
 def test_out_of_range_rejected(field, value):
