@@ -83,7 +83,17 @@ class WccGraph:
     def nnz(self) -> int:
         return wcc_graph_nnz(self.handle)
 
-    def csr(self):
+    def csr(self, device: bool = False):
+        """The graph's CSR (row offsets, columns): numpy arrays, or CUDA
+        tensors on the current device when ``device``."""
+        if device:
+            import torch
+            off = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+            adj = torch.empty(max(self.nnz, 1), dtype=torch.int32, device="cuda")
+            wcc_graph_export_csr(self.handle, off.data_ptr(), adj.data_ptr(), 1,
+                                 torch.cuda.current_stream().cuda_stream)
+            torch.cuda.current_stream().synchronize()
+            return off, adj[:self.nnz]
         off = np.empty(self.n + 1, np.int64)
         adj = np.empty(max(self.nnz, 1), np.int32)
         wcc_graph_export_csr(self.handle, off.ctypes.data, adj.ctypes.data, 0, 0)

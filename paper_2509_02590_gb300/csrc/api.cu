@@ -186,6 +186,19 @@ int tiny_max_deg_config() {
   return (int)(v < 0 ? 0 : v > (1ll << 30) ? (1ll << 30) : v);
 }
 
+// CSR builder of wcc_create_graph_from_edges (WCC_CSR_BUILDER): "rows" sorts
+// every row on chip (and sorts all entries at once when a row is too long
+// for that); "radix" always sorts all entries at once; "auto" (the default)
+// takes the rows for edge lists of up to CSR_ROWS_AUTO_MAX_EDGES edges.  Both
+// give the same CSR.
+constexpr int64_t CSR_ROWS_AUTO_MAX_EDGES = 1ll << 24;
+bool csr_rows_config(int64_t m) {
+  const char *e = getenv("WCC_CSR_BUILDER");
+  if (e && strcmp(e, "rows") == 0) return true;
+  if (e && strcmp(e, "radix") == 0) return false;
+  return m <= CSR_ROWS_AUTO_MAX_EDGES;
+}
+
 // Dynamic shared memory per refinement CTA (WCC_SMEM_KB, default: the
 // largest a CTA can opt into, one CTA per SM).  Items whose working set is
 // larger use a global slab.
@@ -585,6 +598,14 @@ Graph *build_from_edges(const int32_t *src, const int32_t *dst, int64_t m, int64
   int64_t *d_off = static_cast<int64_t *>(g->off.ensure(8 * (n + 1)));
   WCC_CUDA(cudaMemsetAsync(d_off, 0, 8 * (n + 1), s));
   int64_t nnz = 0;
+  if (m > 0 && csr_rows_config(m)) {
+    DevBuf rbufs[CSR_ROW_BUFS];
+    if (csr_by_rows(d_src, d_dst, m, n, d_off, g->adj, &nnz, rbufs, s)) {
+      g->nnz = nnz;
+      return g.release();
+    }
+    WCC_CUDA(cudaMemsetAsync(d_off, 0, 8 * (n + 1), s));  // the degree counts start at zero
+  }
   if (m > 0) {
     // the columns get room for every directed entry, so nothing has to be
     // read back before the end: one read of {error, nnz} closes the build

@@ -62,6 +62,17 @@ struct Workspace {
   uint32_t *sk = nullptr, *sv = nullptr;
 };
 
+// ---- csr.cu ----------------------------------------------------------------
+// CSR of an edge list by rows (count, scatter, sort every row on chip, pack),
+// for graphs whose longest row fits one CTA's shared memory.  Fills off[0..n]
+// and adj_buf (room for 2m entries) and returns true; returns false when a
+// row is too long, leaving off and adj_buf with unspecified contents (the
+// caller then sorts all entries).  An endpoint outside [0, n) fails with
+// WCC_ERR_INVALID.  `b`: its temporaries, grown on demand.
+constexpr int CSR_ROW_BUFS = 7;
+bool csr_by_rows(const int32_t *src, const int32_t *dst, int64_t m, int64_t n, int64_t *off,
+                 DevBuf &adj_buf, int64_t *nnz_out, DevBuf (&b)[CSR_ROW_BUFS], cudaStream_t s);
+
 // ---- graph ----------------------------------------------------------------
 struct Graph {
   int64_t n = 0;

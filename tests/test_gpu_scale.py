@@ -117,6 +117,34 @@ def test_dcpp_10m_repeated_runs_identical(dcpp10m):
         assert np.array_equal(out_p.numpy(), ref)
 
 
+def test_dcpp_10m_csr_builders_agree(dcpp10m, monkeypatch):
+    """The 10M-vertex, 200M-edge graph's CSR is the same from both builders
+    (rows sorted on chip, which hands the graph to the full sort if a row is
+    longer than one CTA sorts; all 400M directed entries sorted at once),
+    and it is a simple symmetric graph: rows strictly ascending, no
+    self-loop, and the reversed entries form the same set."""
+    wcc = _wcc()
+    w = dcpp10m
+    monkeypatch.setenv("WCC_CSR_BUILDER", "rows")
+    with wcc.WccGraph.from_edges(w.src, w.dst, w.n) as g:
+        off_r, adj_r = g.csr(device=True)
+    monkeypatch.setenv("WCC_CSR_BUILDER", "radix")
+    with wcc.WccGraph.from_edges(w.src, w.dst, w.n) as g:
+        off_x, adj_x = g.csr(device=True)
+    assert torch.equal(off_r, off_x)
+    assert torch.equal(adj_r, adj_x)
+    del off_x, adj_x
+    deg = off_r[1:] - off_r[:-1]
+    row = torch.repeat_interleave(torch.arange(w.n, device=adj_r.device, dtype=torch.int64), deg)
+    col = adj_r.long()
+    assert bool((row != col).all())
+    same_row = row[1:] == row[:-1]
+    assert bool((col[1:][same_row] > col[:-1][same_row]).all())
+    fwd = torch.sort(row * w.n + col).values
+    rev = torch.sort(col * w.n + row).values
+    assert torch.equal(fwd, rev)
+
+
 def test_dcpp_10m_500k_clusters_sampled_parity():
     """The second reading of the 10M-vertex configuration: 500k clusters of
     mean size 20."""
