@@ -987,6 +987,7 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
       // (rows may sit in the global slab, where each dependent load costs
       // an L2 round trip).
       int pf_x = -1, pf_b = 0, pf_e = 0, pf_j = 0;
+      const bool adj_global = __isGlobal(m.adj);
       for (int step = 0; step < nsv; ++step) {
         if (X < 0) {
           if (lane == 0) atomicOr(err, DERR_INTERNAL);
@@ -1008,6 +1009,15 @@ __device__ __forceinline__ bool ma_pass_first(const RefineParams &P, const Mem<I
         if (step == nsv - 1) break;
         const bool hit = X == pf_x;
         const int b = hit ? pf_b : m.off[X], e = hit ? pf_e : m.off[X + 1];
+        if (adj_global) {
+          // rows of the next ids follow this one in memory, and the next
+          // vertex is most often the next id of its level: ask L1 for the
+          // lines ahead
+          constexpr int PER_LINE = 128 / (int)sizeof(IT);
+          const long long qa = (long long)b + (long long)PER_LINE * (lane + 1);
+          const IT *pa = m.adj + (qa < E ? qa : E - 1);
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(pa));
+        }
         const int p1 = X + 1, w1 = p1 >> 5;
         const int ia = w1 + lane, ib = w1 + 32 + lane;
         const uint32_t sa = ia < W ? bm[top * W + ia] : 0u, sb = ib < W ? bm[top * W + ib] : 0u;
