@@ -20,6 +20,7 @@ Workloads (--workload; the default is the one the driver times):
   dcpp_10m   degree-corrected planted partition, 10M vertices, ~200M edges,
              power-law cluster sizes 10-50,000 (exponent 1.8), 5% chain clusters;
   dcpp_10m_b the same with 500k clusters (size exponent fitted to a mean of 20);
+  dcpp_1m    the laws of dcpp_10m at 1M vertices, ~20M edges (a profiling case);
   dcpp_100m  100M vertices, ~2B edges, 5M clusters on [10, 100,000], 3%
              bridged two-part clusters (about 100 GB of device memory).
 The two large ones are generated on the GPU and run with the schedule tuning
@@ -49,8 +50,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "WCC clusters/s and edges/s at 1 GB300 (batched/served vs plain), %HBM roofline; p50/p99"
-WORKLOADS = ("lfr_100k", "planted_1k", "dcpp_10m", "dcpp_10m_b", "dcpp_100m")
-LARGE = ("dcpp_10m", "dcpp_10m_b", "dcpp_100m")
+WORKLOADS = ("lfr_100k", "planted_1k", "dcpp_1m", "dcpp_10m", "dcpp_10m_b", "dcpp_100m")
+LARGE = ("dcpp_1m", "dcpp_10m", "dcpp_10m_b", "dcpp_100m")
 
 
 def workload(name: str, rank: int):
@@ -64,6 +65,8 @@ def workload(name: str, rank: int):
         return gpu_graphs.dcpp_10m(seed=rank)
     if name == "dcpp_10m_b":
         return gpu_graphs.dcpp_10m_b(seed=rank)
+    if name == "dcpp_1m":
+        return gpu_graphs.dcpp_1m(seed=rank)
     return gpu_graphs.dcpp_100m(seed=rank)
 
 
@@ -79,6 +82,8 @@ def describe(name: str, w) -> dict:
                       "halves, 10 pendant vertices)",
         "dcpp_10m": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected edges, "
                     f"{n_clusters(w)} clusters (sizes 10-50,000, 5% chains of 2-4 parts)",
+        "dcpp_1m": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected edges, "
+                   f"{n_clusters(w)} clusters (the 10M graph's laws at a tenth of its size)",
         "dcpp_10m_b": f"degree-corrected planted partition, {w.n} vertices, {w.m} undirected "
                       f"edges, {n_clusters(w)} clusters (sizes 10-50,000 with the exponent fitted "
                       "to a mean of 20, 5% chains of 2-4 parts)",

@@ -201,6 +201,15 @@ def dcpp_10m(seed: int = 0, device: str = "cuda") -> GpuWorkload:
                           chain_parts=(2, 4), device=device, draw_factor=1.285)
 
 
+def dcpp_1m(seed: int = 0, device: str = "cuda") -> GpuWorkload:
+    """The laws of dcpp_10m at a tenth of the size: 1M vertices, about 20M
+    undirected edges, cluster sizes on [10, 50000] (a case small enough for
+    a profiler capture of one refinement launch)."""
+    return dc_planted_gpu(1_000_000, 20_000_000, seed=seed, deg_exp=2.2, size_exp=1.8,
+                          size_min=10, size_max=50_000, f_in=0.8, chain_frac=0.05,
+                          chain_parts=(2, 4), device=device, draw_factor=1.285)
+
+
 def dcpp_100m(seed: int = 0, device: str = "cuda") -> GpuWorkload:
     """100M vertices, about 2B undirected edges (Chung-Lu exponent 2.1,
     maximum degree 200k), cluster sizes on [10, 100000] with the exponent
