@@ -77,6 +77,11 @@ def lib():
         L.wo_wcc.argtypes = [i64, i64p, i32p, i32p, i32, i64, i64, i32, u8p, i64, i32, i32p,
                              ctypes.POINTER(Stats)]
         L.wo_wcc.restype = ctypes.c_int
+        L.wo_cm.argtypes = [i64, i64p, i32p, i32p, i32, i64, i64, i32, i64, i64, u8p, i64, i32,
+                            i32p, ctypes.POINTER(Stats)]
+        L.wo_cm.restype = ctypes.c_int
+        L.wo_cpm_communities.argtypes = [i64, i64, i32p, i32p, i64, i64, i32, i32p]
+        L.wo_cpm_communities.restype = i64
         _lib = L
     return _lib
 
@@ -171,4 +176,41 @@ def wcc(n: int, off: np.ndarray, adj: np.ndarray, labels: np.ndarray, min_size: 
                       ctypes.byref(st))
     if rc != 0:
         raise RuntimeError(f"wo_wcc failed ({rc})")
+    return out, st.as_dict()
+
+
+def cpm_communities(n: int, eu, ev, gnum: int, gden: int, connected: bool = True) -> np.ndarray:
+    """CPM local moving, then (connected) the connected parts of every
+    community: comm[v] = smallest id of v's community (the community step
+    of CM)."""
+    eu, ev = _edges(eu, ev)
+    comm = np.empty(n, dtype=np.int32)
+    r = lib().wo_cpm_communities(n, len(eu), _p(eu, ctypes.c_int32), _p(ev, ctypes.c_int32),
+                                 gnum, gden, int(bool(connected)), _p(comm, ctypes.c_int32))
+    if r < 0:
+        raise ValueError("bad input")
+    return comm
+
+
+def cm(n: int, off: np.ndarray, adj: np.ndarray, labels: np.ndarray, min_size: int,
+       gnum: int, gden: int, kind: int = RULE_LOG10, num: int = 1, den: int = 1,
+       only_labels: Optional[np.ndarray] = None, out_mode: int = 0):
+    """CM refinement (WCC with the CPM community step after every split).
+    Returns (label_out int32[n], stats dict)."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    assert off.shape == (n + 1,) and labels.shape == (n,)
+    out = np.empty(n, dtype=np.int32)
+    st = Stats()
+    only_p, n_only = None, 0
+    if only_labels is not None:
+        only = np.ascontiguousarray(only_labels, dtype=np.uint8)
+        only_p, n_only = _p(only, ctypes.c_uint8), len(only)
+    adj_p = _p(adj if len(adj) else np.zeros(1, np.int32), ctypes.c_int32)
+    rc = lib().wo_cm(n, _p(off, ctypes.c_int64), adj_p, _p(labels, ctypes.c_int32), kind, num,
+                     den, min_size, gnum, gden, only_p, n_only, out_mode, _p(out, ctypes.c_int32),
+                     ctypes.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"wo_cm failed ({rc})")
     return out, st.as_dict()

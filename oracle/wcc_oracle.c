@@ -484,11 +484,106 @@ static int cmp_vset_min(const void *a, const void *b) {
   return (x->v[0] > y->v[0]) - (x->v[0] < y->v[0]);
 }
 
+/* ------------------------------------------------------------------------ */
+/* GetCommunities (Algorithm 5) with a CPM community detection step.  The
+ * Constant Potts Model scores a partition P of the part's vertices as
+ *   Q(P) = sum over communities c of [ e_c - gamma * n_c (n_c - 1) / 2 ],
+ * e_c the edges inside c, n_c its size, gamma = gnum / gden (Section 3 runs
+ * Leiden with this quality).  Local moving from singletons: sweeps over the
+ * vertices in ascending local id, at most CPM_MAX_SWEEPS of them, stopping
+ * after a sweep that moves nothing.  For vertex v, taken out of its
+ * community c0, joining community c gains (scaled by gden)
+ *   g(c) = k(v, c) * gden - gnum * n_c,
+ * k(v, c) = edges from v into c and n_c counted without v; joining an
+ * empty community gains 0.  The candidates are the communities of v's
+ * neighbours other than c0 and, when c0 holds more than v, the empty
+ * community numbered n + v (community ids are 0..2n-1; v starts in v).  The
+ * best candidate has the largest gain, ties to the smallest community id; v
+ * moves there only when that gain is strictly above g(c0), so every move
+ * raises Q and the sweeps end.  Finally (connected != 0, as CM uses it)
+ * every community is split into its connected parts (edges inside the
+ * community), so that every community handed on is connected.  comm[v] =
+ * smallest local id of v's final community.  Returns the number of
+ * communities. */
+#define CPM_MAX_SWEEPS 64
+
+static int32_t cpm_communities(const lgraph *H, int64_t gnum, int64_t gden, int32_t connected,
+                               int32_t *comm) {
+  const int32_t n = H->n;
+  int32_t *c = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+  int64_t *size = (int64_t *)calloc(2 * (size_t)n + 1, sizeof(int64_t));
+  int64_t *k = (int64_t *)calloc(2 * (size_t)n + 1, sizeof(int64_t));
+  int32_t i, v, sweep, count;
+  int64_t q;
+  for (v = 0; v < n; v++) {
+    c[v] = v;
+    size[v] = 1;
+  }
+  for (sweep = 0; sweep < CPM_MAX_SWEEPS; sweep++) {
+    int32_t moved = 0;
+    for (v = 0; v < n; v++) {
+      const int32_t c0 = c[v];
+      int32_t best = -1;
+      int64_t bestg = 0, g0;
+      for (q = H->off[v]; q < H->off[v + 1]; q++) k[c[H->adj[q]]]++;
+      size[c0]--; /* v taken out of c0 */
+      g0 = k[c0] * gden - gnum * size[c0];
+      for (q = H->off[v]; q < H->off[v + 1]; q++) {
+        const int32_t cu = c[H->adj[q]];
+        int64_t g;
+        if (cu == c0) continue;
+        g = k[cu] * gden - gnum * size[cu];
+        if (best < 0 || g > bestg || (g == bestg && cu < best)) {
+          best = cu;
+          bestg = g;
+        }
+      }
+      if (size[c0] > 0) { /* the empty community n + v */
+        const int32_t ce = n + v;
+        if (best < 0 || 0 > bestg || (0 == bestg && ce < best)) {
+          best = ce;
+          bestg = 0;
+        }
+      }
+      for (q = H->off[v]; q < H->off[v + 1]; q++) k[c[H->adj[q]]] = 0;
+      if (best >= 0 && bestg > g0) {
+        c[v] = best;
+        size[best]++;
+        moved++;
+      } else {
+        size[c0]++;
+      }
+    }
+    if (moved == 0) break;
+  }
+  /* connected parts of every community: union-find over the edges inside
+   * a community, root = smallest local id */
+  for (v = 0; v < n; v++) comm[v] = v;
+  for (v = 0; v < n; v++) {
+    if (!connected) { /* the local-moving communities themselves */
+      for (i = v + 1; i < n; i++)
+        if (c[i] == c[v]) uf_union(comm, i, v);
+      continue;
+    }
+    for (q = H->off[v]; q < H->off[v + 1]; q++) {
+      const int32_t u = H->adj[q];
+      if (c[u] == c[v]) uf_union(comm, u, v);
+    }
+  }
+  count = 0;
+  for (i = 0; i < n; i++) {
+    comm[i] = uf_find(comm, i);
+    count += comm[i] == i;
+  }
+  free(c); free(size); free(k);
+  return count;
+}
+
 /* One work item (Algorithm 3, with the peel and the connectivity check in
  * front of the cut): S is connected-or-not, ascending. */
 static int process_item(const graph *G, const int32_t *S, int32_t n, int32_t *pos,
-                        int32_t kind, int64_t num, int64_t den, int32_t min_size, vlist *Q,
-                        vlist *W, wo_stats *st) {
+                        int32_t kind, int64_t num, int64_t den, int32_t min_size, int32_t cm,
+                        int64_t gnum, int64_t gden, vlist *Q, vlist *W, wo_stats *st) {
   lgraph H, H1;
   uint8_t *alive, *side;
   int32_t *S1, *comp, *rep, *part0, *part1;
@@ -537,8 +632,28 @@ static int process_item(const graph *G, const int32_t *S, int32_t n, int32_t *po
       if (side[i]) part1[n1++] = S1[i];
       else part0[n0++] = S1[i];
     }
-    if (n0 >= min_size) vlist_push(Q, part0, n0);
-    if (n1 >= min_size) vlist_push(Q, part1, n1);
+    if (!cm) {
+      if (n0 >= min_size) vlist_push(Q, part0, n0);
+      if (n1 >= min_size) vlist_push(Q, part1, n1);
+    } else {
+      /* CMC (Algorithm 5): each part above s_post goes through
+       * GetCommunities, and every community above s_post is checked again
+       * (one community is the whole part, checked again as one unit) */
+      int32_t p;
+      for (p = 0; p < 2; p++) {
+        const int32_t *P = p ? part1 : part0;
+        const int32_t np_ = p ? n1 : n0;
+        lgraph HP;
+        int32_t *cm_comm;
+        if (np_ < min_size) continue;
+        induce(G, P, np_, pos, &HP);
+        cm_comm = (int32_t *)malloc(sizeof(int32_t) * (size_t)np_);
+        cpm_communities(&HP, gnum, gden, 1, cm_comm);
+        push_components(Q, P, cm_comm, np_, min_size);
+        free(cm_comm);
+        lgraph_free(&HP);
+      }
+    }
     free(part0); free(part1);
   } else {
     rc = -2;
@@ -548,10 +663,10 @@ static int process_item(const graph *G, const int32_t *S, int32_t n, int32_t *po
   return rc;
 }
 
-int wo_wcc(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *label_in,
-           int32_t kind, int64_t num, int64_t den, int32_t min_size,
-           const uint8_t *only_label, int64_t n_only, int32_t out_mode,
-           int32_t *label_out, wo_stats *stats) {
+static int refine_all(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *label_in,
+                      int32_t kind, int64_t num, int64_t den, int32_t min_size, int32_t cm,
+                      int64_t gnum, int64_t gden, const uint8_t *only_label, int64_t n_only,
+                      int32_t out_mode, int32_t *label_out, wo_stats *stats) {
   graph G;
   wo_stats st;
   lv_pair *pairs;
@@ -599,7 +714,8 @@ int wo_wcc(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *lab
   /* WCC (Algorithm 2) / isWCC (Algorithm 3): drain the queue */
   while (Q.len > 0 && rc == 0) {
     vset it = Q.a[--Q.len];
-    rc = process_item(&G, it.v, it.n, pos, kind, num, den, min_size, &Q, &W, &st);
+    rc = process_item(&G, it.v, it.n, pos, kind, num, den, min_size, cm, gnum, gden, &Q, &W,
+                      &st);
     free(it.v);
   }
 
@@ -617,4 +733,34 @@ int wo_wcc(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *lab
   free(pairs); free(pos); free(S); free(comp);
   if (stats) *stats = st;
   return rc;
+}
+
+int wo_wcc(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *label_in,
+           int32_t kind, int64_t num, int64_t den, int32_t min_size,
+           const uint8_t *only_label, int64_t n_only, int32_t out_mode,
+           int32_t *label_out, wo_stats *stats) {
+  return refine_all(n, off, adj, label_in, kind, num, den, min_size, 0, 0, 1, only_label, n_only,
+                    out_mode, label_out, stats);
+}
+
+/* CM (Section 2.4, Algorithms 4-5): WCC whose split parts go through the CPM
+ * community step before they are checked again. */
+int wo_cm(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *label_in,
+          int32_t kind, int64_t num, int64_t den, int32_t min_size, int64_t gnum, int64_t gden,
+          const uint8_t *only_label, int64_t n_only, int32_t out_mode, int32_t *label_out,
+          wo_stats *stats) {
+  if (gnum < 0 || gden < 1) return -1;
+  return refine_all(n, off, adj, label_in, kind, num, den, min_size, 1, gnum, gden, only_label,
+                    n_only, out_mode, label_out, stats);
+}
+
+int64_t wo_cpm_communities(int64_t n, int64_t m, const int32_t *eu, const int32_t *ev,
+                           int64_t gnum, int64_t gden, int32_t connected, int32_t *comm) {
+  lgraph H;
+  int64_t r;
+  if (n < 0 || gnum < 0 || gden < 1) return -1;
+  lgraph_from_edges(n, m, eu, ev, NULL, &H);
+  r = cpm_communities(&H, gnum, gden, connected, comm);
+  lgraph_free(&H);
+  return r;
 }

@@ -8,7 +8,8 @@
  *
  * What it computes (paper: Section 2.2 Algorithm 1 "CCR", Section 2.3
  * Algorithms 2-3 "WCC" / "isWCC", criterion f(n) of Section 2 with log10 n as
- * used in Section 3), under these readings where the paper is silent:
+ * used in Section 3; Section 2.4 Algorithms 4-5 "CM" with a CPM community
+ * step), under these readings where the paper is silent:
  *   - threshold: a cluster of n vertices fails iff its min cut <= T(n), with
  *     T(n) the exact integer form of the criterion (floor(log10 n) for LOG10);
  *   - peeling: round-synchronous removal of every vertex whose degree inside
@@ -90,6 +91,29 @@ int wo_wcc(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *lab
            int32_t kind, int64_t num, int64_t den, int32_t min_size,
            const uint8_t *only_label, int64_t n_only, int32_t out_mode,
            int32_t *label_out, wo_stats *stats);
+
+/* The community step of CM (GetCommunities of Algorithm 5) as used here: CPM
+ * local moving at resolution gamma = gnum/gden on a graph given as an edge
+ * list on ids 0..n-1 (each entry counts once), in ascending-id sweeps from
+ * singletons, each vertex moving to the neighbouring (or an empty) community
+ * of largest gain k(v,c)*gden - gnum*n_c (ties to the smallest community id)
+ * only when that beats staying, at most 64 sweeps; then, when connected is
+ * nonzero (as CM uses it), every community is split into its connected
+ * parts.  comm[v] = smallest id of v's community.  Returns the number of
+ * communities, or -1 on bad input. */
+int64_t wo_cpm_communities(int64_t n, int64_t m, const int32_t *eu, const int32_t *ev,
+                           int64_t gnum, int64_t gden, int32_t connected, int32_t *comm);
+
+/* CM refinement (Section 2.4, Algorithms 4-5): wo_wcc, except that each part
+ * of a split with at least min_size vertices is divided into its CPM
+ * communities (wo_cpm_communities on the part's induced subgraph) and every
+ * community with at least min_size vertices is checked again.  Arguments as
+ * wo_wcc, plus the resolution gnum/gden (gnum >= 0, gden >= 1).  Returns 0,
+ * or -1 on bad input. */
+int wo_cm(int64_t n, const int64_t *off, const int32_t *adj, const int32_t *label_in,
+          int32_t kind, int64_t num, int64_t den, int32_t min_size, int64_t gnum, int64_t gden,
+          const uint8_t *only_label, int64_t n_only, int32_t out_mode, int32_t *label_out,
+          wo_stats *stats);
 
 #ifdef __cplusplus
 }
