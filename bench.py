@@ -516,6 +516,33 @@ def large_record(wcc, torch, dev, flush, stream, peak, peak_kind, name="dcpp_10m
     return rec
 
 
+# ------------------------------------------------------------------ CM
+def cm_record(wcc, torch, w, src_d, dst_d, lab_d, flush, runs=5):
+    """CM (WCC whose split parts go through the CPM community step) on the
+    workload's resident graph at the two resolutions the paper's inputs use
+    (CPM 0.001 and 0.01): mean time per run, edges/s, and the counters."""
+    out = torch.empty_like(lab_d)
+    rec = {"runs": runs}
+    with wcc.WccGraph.from_edges(src_d, dst_d, w.n) as g:
+        for gnum, gden in ((1, 1000), (1, 100)):
+            for _ in range(2):
+                g.run_cm(lab_d, (gnum, gden), min_size=w.min_size, out=out)
+            ts, st = [], None
+            for k in range(runs):
+                flush.fill_(k & 0xff)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                _, st = g.run_cm(lab_d, (gnum, gden), min_size=w.min_size, out=out, stats=True)
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = sum(ts) / len(ts)
+            rec[f"cpm_{gnum}/{gden}"] = {
+                "ms_per_run": ms, "edges_per_s": w.m / (ms / 1e3),
+                "items": st["items"], "splits": st["splits"], "out_clusters": st["out_clusters"]}
+    return rec
+
+
 # ------------------------------------------------------------------ ranks
 def aggregate_ranks(dist, torch, dev, total_ms: float, m: int, clusters: int):
     """Weak scaling across ranks: every rank refines its own instance with no
@@ -644,6 +671,8 @@ def main():
     ap.add_argument("--serving-pool", type=int, default=200)
     ap.add_argument("--no-autotune", action="store_true",
                     help="run the large configurations with the default tuning")
+    ap.add_argument("--no-cm", action="store_true",
+                    help="skip the CM record (the CPM community step after every split)")
     ap.add_argument("--no-large-record", action="store_true",
                     help="skip the bounded 10M-vertex record beside the default workload")
     args = ap.parse_args()
@@ -816,6 +845,13 @@ def main():
         except Exception as e:  # the headline stands on its own
             large_rec = {"error": f"{type(e).__name__}: {e}"[:300]}
 
+    cm = None
+    if name in ("lfr_100k", "planted_1k") and not args.no_cm:
+        try:
+            cm = cm_record(wcc, torch, w, src_d, dst_d, lab_d, flush)
+        except Exception as e:  # the headline stands on its own
+            cm = {"error": f"{type(e).__name__}: {e}"[:300]}
+
     serving = None
     if args.serving_requests > 0 and name == "lfr_100k":
         serving = serving_bench(wcc, np, torch, n_requests=args.serving_requests,
@@ -839,7 +875,7 @@ def main():
                         "d2h_bytes_per_step": int(4 * w.n), "ms_per_step": 1e3 * e2e_mean,
                         "steps": len(e2e_t), "matches_device_run": ok},
                 "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
-                "dcpp_10m": large_rec, "serving": serving}
+                "dcpp_10m": large_rec, "cm": cm, "serving": serving}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(name, w)
         print(json.dumps(line), flush=True)

@@ -144,6 +144,24 @@ int wcc_run(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshol
             int32_t min_size, int32_t mode, int32_t *clustering_out, int on_device, void *stream,
             wcc_stats *stats);
 
+/* CM refinement (Section 2.4, Algorithms 4-5): wcc_run in BATCHED mode,
+ * except that each part of a cut split with at least min_size vertices first
+ * goes through the community step (GetCommunities of Algorithm 5), and every
+ * community of at least min_size vertices is checked again (peel,
+ * connectivity, cut) like any other part.  The community step is CPM local
+ * moving at resolution cpm_num / cpm_den on the part's induced subgraph:
+ * sweeps over the part's vertices in ascending id, from singletons, at most
+ * 64 sweeps or until one moves nothing; a vertex taken out of its community
+ * c0 joins the neighbouring community c of largest gain
+ * k(v,c) * cpm_den - cpm_num * |c| (or an empty community, gain 0), ties to
+ * the smallest community id, and only when that gain beats staying in c0;
+ * then every community is split into its connected parts.  Arguments,
+ * layouts and results as wcc_run.  WCC_ERR_INVALID unless
+ * 0 <= cpm_num <= 2^31 and 1 <= cpm_den <= 2^31. */
+int wcc_run_cm(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+               int32_t min_size, int64_t cpm_num, int64_t cpm_den, int32_t *clustering_out,
+               int on_device, void *stream, wcc_stats *stats);
+
 /* Release a graph (NULL is ignored). */
 void wcc_destroy_graph(wcc_graph *g);
 

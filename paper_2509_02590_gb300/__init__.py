@@ -17,7 +17,7 @@ from ._binding import (WCC_MODE_BATCHED, WCC_MODE_PLAIN, WCC_RULE_LINEAR,  # noq
                        wcc_build_csr_no_alloc, wcc_create_graph,
                        wcc_create_graph_from_edges, wcc_destroy_graph, wcc_graph_export_csr,
                        wcc_graph_nnz, wcc_graph_num_vertices, wcc_kernel_launches, wcc_device_allocations,
-                       wcc_last_error, wcc_poll, wcc_run, wcc_server_create,
+                       wcc_last_error, wcc_poll, wcc_run, wcc_run_cm, wcc_server_create,
                        wcc_server_destroy, wcc_submit, wcc_wait,
                        wcc_stats, wcc_threshold_rule, wcc_tuning, wcc_get_tuning,
                        wcc_set_tuning, wcc_autotune, wcc_load_tuning, wcc_job_start,
@@ -118,6 +118,28 @@ class WccGraph:
         r = rule_struct(rule, num, den)
         m = _MODES[mode] if isinstance(mode, str) else int(mode)
         wcc_run(self.handle, pin, r, min_size, m, pout, dev, stream, st)
+        if out is not kout and not _is_torch(out):
+            out[...] = kout
+        return (out, st.as_dict()) if stats else out
+
+    def run_cm(self, labels, resolution=(1, 1000), min_size: int = 2, rule="log10",
+               num: int = 1, den: int = 1, out=None, stats: bool = False):
+        """CM refinement (WCC whose split parts go through the CPM community
+        step at resolution = (cpm_num, cpm_den)); buffers as ``run``."""
+        pin, dev, stream, kin = _buf(labels, np.int32)
+        if out is None:
+            if _is_torch(labels):
+                import torch
+                out = torch.empty_like(labels)
+            else:
+                out = np.empty(len(kin), np.int32)
+        pout, dev_o, _, kout = _buf(out, np.int32)
+        if dev_o != dev:
+            raise TypeError("labels and out must both be host or both be device buffers")
+        st = wcc_stats() if stats else None
+        r = rule_struct(rule, num, den)
+        gnum, gden = resolution
+        wcc_run_cm(self.handle, pin, r, min_size, int(gnum), int(gden), pout, dev, stream, st)
         if out is not kout and not _is_torch(out):
             out[...] = kout
         return (out, st.as_dict()) if stats else out

@@ -90,6 +90,9 @@ def _load():
     L.wcc_run.argtypes = [vp, vp, ctypes.POINTER(wcc_threshold_rule), i32, i32, vp, c_int, vp,
                           ctypes.POINTER(wcc_stats)]
     L.wcc_run.restype = c_int
+    L.wcc_run_cm.argtypes = [vp, vp, ctypes.POINTER(wcc_threshold_rule), i32, i64, i64, vp, c_int,
+                             vp, ctypes.POINTER(wcc_stats)]
+    L.wcc_run_cm.restype = c_int
     L.wcc_destroy_graph.argtypes = [vp]
     L.wcc_destroy_graph.restype = None
     L.wcc_server_create.argtypes = [i64, gpp]
@@ -267,6 +270,14 @@ def wcc_run(g: int, clustering_in: int, rule: wcc_threshold_rule | None, min_siz
     _check(lib.wcc_run(g, clustering_in, ctypes.byref(rule) if rule is not None else None,
                        min_size, mode, clustering_out, on_device, stream,
                        ctypes.byref(stats) if stats is not None else None))
+
+
+def wcc_run_cm(g: int, clustering_in: int, rule: wcc_threshold_rule | None, min_size: int,
+               cpm_num: int, cpm_den: int, clustering_out: int, on_device: int, stream: int,
+               stats: wcc_stats | None = None) -> None:
+    _check(lib.wcc_run_cm(g, clustering_in, ctypes.byref(rule) if rule is not None else None,
+                          min_size, cpm_num, cpm_den, clustering_out, on_device, stream,
+                          ctypes.byref(stats) if stats is not None else None))
 
 
 def wcc_destroy_graph(g: int) -> None:

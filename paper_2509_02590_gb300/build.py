@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwcc_gb300.so")
-SOURCES = ["api.cu", "refine.cu", "primitives.cu", "pipeline.cu", "server.cu", "job.cu", "csr.cu"]
+SOURCES = ["api.cu", "refine.cu", "primitives.cu", "pipeline.cu", "server.cu", "job.cu", "csr.cu", "cm.cu"]
 HEADERS = ["common.cuh", "internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -385,11 +385,19 @@ struct Timer {
 };
 
 
-enum RunBuf { R_IN, R_OUT, R_POOL, R_SLOT, R_LMIN, R_RING, R_CTR, R_SLAB, R_REQ, R_INH, R_COUNT };
+enum RunBuf { R_IN, R_OUT, R_POOL, R_SLOT, R_LMIN, R_RING, R_CTR, R_SLAB, R_REQ, R_INH,
+              R_CM_PARTS, R_CM_PARTOF, R_CM_SCRATCH, R_CM_ITEMS, R_CM_MISC, R_COUNT };
+static_assert(R_COUNT <= 16, "Graph::rb holds 16 buffers");
+
+// CM (Section 2.4, Algorithms 4-5): the resolution of its CPM community step.
+struct CmOpts {
+  int64_t gnum, gden;
+};
 static_assert(R_COUNT <= 16, "run buffers");
 
 void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, int32_t min_size,
-              int32_t mode, int32_t *lab_out, int on_device, cudaStream_t s, wcc_stats *stats) {
+              int32_t mode, int32_t *lab_out, int on_device, cudaStream_t s, wcc_stats *stats,
+              const CmOpts *cm = nullptr) {
   auto t_start = std::chrono::steady_clock::now();
   const int64_t n = g->n;
   const wcc_threshold_rule r = checked_rule(rule);
@@ -481,7 +489,34 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
       p.prof_cta = static_cast<CtaProf *>(prof_cta_buf.ensure(sizeof(CtaProf) * (size_t)grid));
       WCC_CUDA(cudaMemsetAsync(p.prof_cta, 0, sizeof(CtaProf) * (size_t)grid, s));
     }
-    if (mode == WCC_MODE_BATCHED) {
+    if (mode == WCC_MODE_BATCHED && cm) {
+      // CM: the sides of every cut split are parked; after each run the
+      // community step publishes their communities and the kernel runs again
+      p.slab = static_cast<char *>(rb[R_SLAB].ensure(slab_bytes * (size_t)grid));
+      p.single_item = 0;
+      p.tickets = 1;
+      p.tiny_max = 0;  // every item on a whole CTA, where the split is parked
+      p.cm = 1;
+      p.cda_cap = (unsigned long long)n + 1024;
+      p.cda = static_cast<Item *>(rb[R_CM_PARTS].ensure(sizeof(Item) * p.cda_cap + 64));
+      p.cda_count = reinterpret_cast<unsigned long long *>(
+          static_cast<char *>(rb[R_CM_PARTS].p) + sizeof(Item) * p.cda_cap);
+      int32_t *partof = static_cast<int32_t *>(rb[R_CM_PARTOF].ensure(8 * (size_t)n));
+      WCC_CUDA(cudaMemsetAsync(partof, 0xff, 8 * (size_t)n, s));
+      for (;;) {
+        WCC_CUDA(cudaMemsetAsync(p.cda_count, 0, sizeof(unsigned long long), s));
+        launch_refine(p, grid, true, s);
+        const RunCounters c = read_back(ctr, s);
+        if (c.error) break;  // reported below
+        const unsigned long long parked = read_back(p.cda_count, s);
+        if (parked == 0) break;
+        const unsigned long long added =
+            cm_round(p.cda, parked, req, cm->gnum, cm->gden, partof, partof + n, n, gi.max_n,
+                     gi.max_dsum, ctr, ring, cap, grid, rb[R_CM_SCRATCH], rb[R_CM_ITEMS],
+                     rb[R_CM_MISC], s);
+        if (added == 0) break;
+      }
+    } else if (mode == WCC_MODE_BATCHED) {
       p.slab = static_cast<char *>(rb[R_SLAB].ensure(slab_bytes * (size_t)grid));
       p.single_item = 0;
       p.tickets = 1;  // nothing is added while the run lasts
@@ -931,6 +966,22 @@ int wcc_run(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshol
     DeviceGuard dg(g->g->device);
     run_impl(g->g, clustering_in, rule, min_size, mode, clustering_out, on_device,
              (cudaStream_t)stream, stats);
+  });
+}
+
+int wcc_run_cm(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
+               int32_t min_size, int64_t cpm_num, int64_t cpm_den, int32_t *clustering_out,
+               int on_device, void *stream, wcc_stats *stats) {
+  return guarded([&] {
+    if (!g) fail(WCC_ERR_INVALID, "graph is NULL");
+    if (cpm_num < 0 || cpm_den < 1 || cpm_num > (1ll << 31) || cpm_den > (1ll << 31))
+      fail(WCC_ERR_INVALID, "the resolution must be cpm_num / cpm_den with 0 <= cpm_num <= 2^31 "
+                            "and 1 <= cpm_den <= 2^31");
+    std::lock_guard<std::mutex> lk(g->g->run_mutex);
+    DeviceGuard dg(g->g->device);
+    const CmOpts o{cpm_num, cpm_den};
+    run_impl(g->g, clustering_in, rule, min_size, WCC_MODE_BATCHED, clustering_out, on_device,
+             (cudaStream_t)stream, stats, &o);
   });
 }
 

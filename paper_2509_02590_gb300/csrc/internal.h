@@ -180,6 +180,12 @@ struct RefineParams {
   CtaProf *prof_cta;          // with prof: one entry per CTA
   unsigned prof_cap;
   unsigned *prof_count;
+  // CM (Algorithm 5): the sides of a cut split are written to the pool and
+  // listed here for the community step instead of being published
+  int cm;
+  Item *cda;
+  unsigned long long *cda_count;
+  unsigned long long cda_cap;
 };
 
 // Bytes of working memory an item of n vertices and at most e local
@@ -270,6 +276,21 @@ T read_back(const T *dev, cudaStream_t s) {
   WCC_CUDA(cudaStreamSynchronize(s));
   return h;
 }
+
+// ---- cm.cu ----------------------------------------------------------------
+// The community step of CM over the parts a refinement run parked
+// (RefineParams::cda, nparts of them): CPM local moving at gnum/gden and the
+// connected parts of every community, written back to the pool; the
+// communities of at least min_size members are reserved at the queue's tail
+// (head reset to it), their slots set and published.  partof / loc: int32
+// [n_vertices], -1 on entry and on return.  max_n / max_dsum bound a part's
+// size and degree sum (those of the largest input cluster).  Returns the
+// number of items published.
+unsigned long long cm_round(const Item *parts, unsigned long long nparts, ReqCtx *reqs,
+                            int64_t gnum, int64_t gden, int32_t *partof, int32_t *loc,
+                            int64_t n_vertices, int64_t max_n, int64_t max_dsum, RunCounters *ctr,
+                            QSlot *ring, uint64_t cap, int grid_max, DevBuf &scratch,
+                            DevBuf &items, DevBuf &misc, cudaStream_t s);
 
 }  // namespace wccg
 

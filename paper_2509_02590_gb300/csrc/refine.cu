@@ -572,6 +572,50 @@ __device__ __forceinline__ int emit_children(const RefineParams &P, const ReqCtx
   return L;
 }
 
+// CM (Algorithm 5): the two sides of a cut split (tag 0 / 1, -1 = not a
+// member) with at least min_size members are written to the item's pool
+// range in ascending local order, side 0 first, and listed in P.cda for the
+// community step, which runs after the kernel; nothing is published.
+template <typename IT>
+__device__ __forceinline__ void park_sides(const RefineParams &P, const ReqCtx &R, uint16_t req,
+                                           const Mem<IT> &m, const int32_t *tag, int n,
+                                           int64_t vbeg, Sh &sh) {
+  int a0 = 0, a1 = 0;
+  for (int i = threadIdx.x; i < n; i += RB) {
+    a0 += tag[i] == 0;
+    a1 += tag[i] == 1;
+  }
+  const int c0 = block_sum_int(a0, sh);
+  const int c1 = block_sum_int(a1, sh);
+  const bool k0 = c0 >= R.min_size, k1 = c1 >= R.min_size;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned lt = lanemask_lt();
+    int r0 = 0, r1 = 0;
+    for (int b = 0; b < n; b += 32) {
+      const int i = b + lane;
+      const int t = i < n ? tag[i] : -1;
+      const bool w0 = k0 && t == 0, w1 = k1 && t == 1;
+      const unsigned m0 = __ballot_sync(FULL, w0), m1 = __ballot_sync(FULL, w1);
+      if (w0) R.pool[vbeg + r0 + __popc(m0 & lt)] = m.gid[i];
+      if (w1) R.pool[vbeg + (k0 ? c0 : 0) + r1 + __popc(m1 & lt)] = m.gid[i];
+      r0 += __popc(m0);
+      r1 += __popc(m1);
+    }
+  }
+  if (threadIdx.x == 0 && (k0 || k1)) {
+    const unsigned long long k = (k0 ? 1ull : 0ull) + (k1 ? 1ull : 0ull);
+    unsigned long long at = atomicAdd(P.cda_count, k);
+    if (at + k > P.cda_cap) {
+      atomicOr(&P.ctr->error, DERR_CAPACITY);
+    } else {
+      if (k0) P.cda[at++] = Item{vbeg, c0, (uint16_t)0, req};
+      if (k1) P.cda[at] = Item{vbeg + (k0 ? c0 : 0), c1, (uint16_t)0, req};
+    }
+  }
+  __syncthreads();
+}
+
 // Continues an item in place as its child L (the component labelled L in
 // tag): every other vertex becomes dead.  Returns the child's size.
 template <typename IT>
@@ -2605,7 +2649,10 @@ __device__ __noinline__ int process_item(const RefineParams &P, unsigned long lo
   if (threadIdx.x == 0) add_ll(&ctr->splits, 1ll);
   for (int i = threadIdx.x; i < n; i += RB) m.B[i] = m.alive[i] ? (m.side[i] ? 1 : 0) : -1;
   __syncthreads();
-  emit_children(P, R, Rg, it.req, m, m.B, n, vb, sh, inh_valid ? ITEM_INH : (uint16_t)0);
+  if (P.cm)
+    park_sides(P, R, it.req, m, m.B, n, vb, sh);
+  else
+    emit_children(P, R, Rg, it.req, m, m.B, n, vb, sh, inh_valid ? ITEM_INH : (uint16_t)0);
   return OUT_CUT_SPLIT;
 }
 
