@@ -473,7 +473,12 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     p.slab_bytes = slab_bytes;
     p.forest_min_n = forest_min_n_config();
     p.dense_max = dense_max_config();
-    p.tiny_max = tiny_max_config();
+    // with no more input clusters than CTAs, every item gets a whole CTA:
+    // one warp per small item only pays off when items outnumber the CTAs
+    // (a 50-vertex item's subtree takes about 2.5 times longer on one warp);
+    // WCC_TINY_N, when set, decides regardless
+    p.tiny_max = (gi.kept <= (int64_t)grid && getenv("WCC_TINY_N") == nullptr) ? 0
+                                                                              : tiny_max_config();
     p.tiny_max_deg = tiny_max_deg_config();
     // optional per-item profile (WCC_PROFILE_ITEMS=<csv path>)
     const char *prof_path = getenv("WCC_PROFILE_ITEMS");

@@ -281,10 +281,13 @@ def _random_workload(seed):
 
 # Internal strategy switches (each must leave the result unchanged): the
 # sparse passes only, the forest acceptance test on every item, working
-# memory in the global slab instead of shared memory, and small items on a
-# whole CTA instead of one warp each.
+# memory in the global slab instead of shared memory, small items on a whole
+# CTA instead of one warp each, and small items forced onto single warps
+# (a run with no more input clusters than CTAs otherwise gives every item a
+# CTA).
 @pytest.mark.parametrize("env", [{"WCC_DENSE_NSV": "0"}, {"WCC_FOREST_MIN_N": "2"},
                                  {"WCC_SMEM_KB": "40"}, {"WCC_TINY_N": "0"},
+                                 {"WCC_TINY_N": "64"}, {"WCC_TINY_N": "32"},
                                  {"WCC_DENSE_NSV": "0", "WCC_FOREST_MIN_N": "2", "WCC_SMEM_KB": "40",
                                   "WCC_TINY_N": "0"}])
 def test_strategy_switches_keep_results(wcc, monkeypatch, env):
