@@ -37,9 +37,10 @@ constexpr int CB = 256;
 constexpr int CPM_MAX_SWEEPS = 64;
 
 // Words of per-part state: gid[n], off[n+1], comm[n], size[2n], kc[2n],
-// uf[n], cnt[n], base[n], adj[d].
+// adj[d] (d local entries).  After the local moving, size holds the
+// union-find and the community sizes, kc the output offsets and indices.
 __host__ __device__ inline size_t cda_words(int64_t n, int64_t d) {
-  return (size_t)(10 * n + 1 + d);
+  return (size_t)(7 * n + 1 + d);
 }
 
 __device__ __forceinline__ int uf_root(int32_t *uf, int x) {
@@ -95,14 +96,20 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
     const int n = it.n;
     const int64_t vbeg = it.vbeg;
     const int min_size = R.min_size;
-    // degree sum bounds the local entries: state in shared memory when it fits
-    long long ds = 0;
+    // the part's members marked, and its local entries counted: the state
+    // lives in shared memory when it fits
     for (int i = threadIdx.x; i < n; i += CB) {
       const int32_t v = R.pool[vbeg + i];
-      ds += R.off[v + 1] - R.off[v];
+      partof[v] = (int32_t)p;
+      loc[v] = i;
     }
     if (threadIdx.x == 0) s_ds = 0;
     __syncthreads();
+    long long ds = 0;
+    for (int i = threadIdx.x; i < n; i += CB) {
+      const int32_t v = R.pool[vbeg + i];
+      for (int64_t q = R.off[v]; q < R.off[v + 1]; ++q) ds += partof[R.adj[q]] == (int32_t)p;
+    }
     atomicAdd(&s_ds, (unsigned long long)ds);
     __syncthreads();
     const size_t need = cda_words(n, (int64_t)s_ds);
@@ -112,22 +119,20 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
     } else if (need <= gwords) {
       ws = gscratch + (size_t)blockIdx.x * gwords;
     } else {
+      for (int i = threadIdx.x; i < n; i += CB) partof[R.pool[vbeg + i]] = -1;
       if (threadIdx.x == 0) atomicOr(err, DERR_CAPACITY);
       __syncthreads();
       continue;
     }
     int32_t *gid = ws, *off = gid + n, *comm = off + n + 1, *size = comm + n, *kc = size + 2 * n;
-    int32_t *uf = kc + 2 * n, *cnt = uf + n, *base = cnt + n, *adj = base + n;
+    int32_t *adj = kc + 2 * n;
+    // after the local moving: union-find and sizes in size[], output
+    // offsets and indices in kc[]
+    int32_t *uf = size, *cnt = size + n, *base = kc, *kidx = kc + n;
+    // the induced subgraph on local ids
     for (int i = threadIdx.x; i < n; i += CB) {
       const int32_t v = R.pool[vbeg + i];
       gid[i] = v;
-      partof[v] = (int32_t)p;
-      loc[v] = i;
-    }
-    __syncthreads();
-    // the induced subgraph on local ids
-    for (int i = threadIdx.x; i < n; i += CB) {
-      const int32_t v = gid[i];
       int d = 0;
       for (int64_t q = R.off[v]; q < R.off[v + 1]; ++q) d += partof[R.adj[q]] == (int32_t)p;
       off[i] = d;
@@ -156,11 +161,14 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
         int moved = 0;
         for (int v = 0; v < n; ++v) {
           const int c0 = comm[v], b = off[v], e = off[v + 1];
+          // the first 32 neighbours' communities stay in a register for the
+          // three passes below (most rows are that short)
+          const int cu0 = b + lane < e ? comm[adj[b + lane]] : -1;
           // neighbours' communities counted, one atomic per community a chunk
           // (most neighbours share a few communities)
           for (int q0 = b; q0 < e; q0 += 32) {
             const int q = q0 + lane;
-            const int cu = q < e ? comm[adj[q]] : -1;
+            const int cu = q0 == b ? cu0 : (q < e ? comm[adj[q]] : -1);
             const unsigned peers = __match_any_sync(FULL, cu);
             if (cu >= 0 && (peers & lanemask_lt()) == 0) atomicAdd(&kc[cu], __popc(peers));
           }
@@ -170,7 +178,7 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
           long long bg = LLONG_MIN;
           int bc = INT_MAX;
           for (int q = b + lane; q < e; q += 32) {
-            const int cu = comm[adj[q]];
+            const int cu = q < b + 32 ? cu0 : comm[adj[q]];
             if (cu == c0) continue;
             const long long g = (long long)kc[cu] * gden - gnum * (long long)size[cu];
             if (g > bg || (g == bg && cu < bc)) {
@@ -185,16 +193,27 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
               bc = ce;
             }
           }
-          for (int o = 16; o > 0; o >>= 1) {
-            const long long og = __shfl_xor_sync(FULL, bg, o);
-            const int oc = __shfl_xor_sync(FULL, bc, o);
-            if (og > bg || (og == bg && oc < bc)) {
-              bg = og;
-              bc = oc;
+          // the warp's best: largest gain (its order-preserving unsigned image
+          // reduced high word, then low word), then the smallest id
+          {
+            const bool has = bc != INT_MAX;
+            const unsigned long long ug = (unsigned long long)bg ^ 0x8000000000000000ull;
+            const unsigned hi = has ? (unsigned)(ug >> 32) : 0u;
+            const unsigned mhi = __reduce_max_sync(FULL, hi);
+            const bool h1 = has && hi == mhi;
+            const unsigned mlo = __reduce_max_sync(FULL, h1 ? (unsigned)ug : 0u);
+            const bool h2 = h1 && (unsigned)ug == mlo;
+            const unsigned mid = __reduce_max_sync(FULL, h2 ? ~(unsigned)bc : 0u);
+            if (__ballot_sync(FULL, has)) {
+              bc = (int)~mid;
+              bg = (long long)((((unsigned long long)mhi << 32) | mlo) ^ 0x8000000000000000ull);
+            } else {
+              bc = INT_MAX;
+              bg = LLONG_MIN;
             }
           }
           __syncwarp();
-          for (int q = b + lane; q < e; q += 32) kc[comm[adj[q]]] = 0;
+          for (int q = b + lane; q < e; q += 32) kc[q < b + 32 ? cu0 : comm[adj[q]]] = 0;
           __syncwarp();
           if (bc != INT_MAX && bg > g0) {
             if (lane == 0) {
@@ -211,7 +230,10 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
     }
     __syncthreads();
     // the connected parts of every community
-    for (int i = threadIdx.x; i < n; i += CB) uf[i] = i;
+    for (int i = threadIdx.x; i < n; i += CB) {
+      uf[i] = i;
+      cnt[i] = 0;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += CB)
       for (int q = off[i]; q < off[i + 1]; ++q) {
@@ -219,24 +241,23 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
         if (u > i && comm[u] == comm[i]) uf_link_min(uf, i, u);
       }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += CB) cnt[i] = 0;
-    __syncthreads();
     for (int i = threadIdx.x; i < n; i += CB) {
       const int r = uf_root(uf, i);
       comm[i] = r;  // comm now holds the root
       atomicAdd(&cnt[r], 1);
     }
     __syncthreads();
-    // kept communities, in ascending root order
+    // kept communities, in ascending root order; uf becomes the running
+    // fill per root
     for (int i = threadIdx.x; i < n; i += CB) {
       const bool keep = comm[i] == i && cnt[i] >= min_size;
       base[i] = keep ? cnt[i] : 0;
-      kc[i] = keep ? 1 : 0;
-      kc[n + i] = 0;  // running fill per root
+      kidx[i] = keep ? 1 : 0;
+      uf[i] = 0;
     }
     __syncthreads();
     block_scan_inplace(base, n, tmp);
-    const int nkeep = block_scan_inplace(kc, n, tmp);
+    const int nkeep = block_scan_inplace(kidx, n, tmp);
     if (threadIdx.x == 0) {
       s_at = atomicAdd(nout, (unsigned long long)nkeep);
       if (s_at + nkeep > out_cap) atomicOr(err, DERR_CAPACITY);
@@ -253,11 +274,11 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
         const int key = kept ? r : -1;
         const unsigned peers = __match_any_sync(FULL, key);
         const int rank = __popc(peers & lanemask_lt());
-        const int before = kept ? kc[n + r] : 0;
+        const int before = kept ? uf[r] : 0;
         __syncwarp();
         if (kept) {
           R.pool[vbeg + base[r] + before + rank] = gid[i];
-          if (rank == 0) kc[n + r] = before + __popc(peers);
+          if (rank == 0) uf[r] = before + __popc(peers);
         }
         __syncwarp();
       }
@@ -266,7 +287,7 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
     if (room)
       for (int i = threadIdx.x; i < n; i += CB)
         if (comm[i] == i && cnt[i] >= min_size)
-          out[at + kc[i]] = Item{vbeg + base[i], cnt[i], (uint16_t)0, it.req};
+          out[at + kidx[i]] = Item{vbeg + base[i], cnt[i], (uint16_t)0, it.req};
     for (int i = threadIdx.x; i < n; i += CB) partof[gid[i]] = -1;
     __syncthreads();
   }
