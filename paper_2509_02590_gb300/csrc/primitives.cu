@@ -120,7 +120,7 @@ void exclusive_scan_impl(const T *in, T *out, int64_t n, T *total, void *temp, c
 // per sort.  Every wait on a predecessor is bounded: past the limit the
 // sort sets DERR_TIMEOUT in *err and leaves its result unspecified.
 
-constexpr int OS_SI = 12;                 // keys per thread
+constexpr int OS_SI = 16;                 // keys per thread (16: 5% faster than 8 or 12 on 400M keys)
 constexpr int OS_TILE = SB * OS_SI;       // keys per tile
 constexpr int OS_MAXPASS = 8;             // 64-bit keys
 constexpr unsigned long long ST_AGG = 1ull << 62, ST_PRE = 2ull << 62;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(SB) k_digit_starts(uint32_t *hist, int npass) 
 }
 
 template <typename K, bool HAS_VAL>
-__global__ void __launch_bounds__(SB) k_onesweep(const K *__restrict__ kin,
+__global__ void __launch_bounds__(SB, 3) k_onesweep(const K *__restrict__ kin,
                                                 const uint32_t *__restrict__ vin,
                                                 K *__restrict__ kout, uint32_t *__restrict__ vout,
                                                 int64_t n, int shift, unsigned tag,
