@@ -25,6 +25,7 @@
 #include <memory>
 #include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "internal.h"
 
@@ -42,8 +43,11 @@ struct Request {
   uint64_t ticket = 0;
   Graph *g = nullptr;
   int64_t n = 0;
-  int32_t *h_in = nullptr;   // pinned copy of the input labels
-  int32_t *h_out = nullptr;  // pinned result
+  // the input labels' copy and the result, in pageable host memory: pinning
+  // or unpinning memory per request (cudaHostAlloc / cudaFreeHost) waits for
+  // the device, and the device runs the open refinement kernel until it
+  // idles, so each submission or collection would stall on the whole load
+  std::vector<int32_t> h_in, h_out;
   // a request that brings its graph as an edge list: the caller's edge
   // buffers (valid until the request is collected), then the graph the
   // server builds from them on admission and owns
@@ -65,10 +69,6 @@ struct Request {
   Workspace ws;
   DevBuf d_in, d_out, pool, vslot, lmin, inh;
   GroupInfo gi{};
-  ~Request() {
-    if (h_in) cudaFreeHost(h_in);
-    if (h_out) cudaFreeHost(h_out);
-  }
   void release_device() {
     for (auto &b : ws.b) b.release();
     d_in.release();
@@ -155,7 +155,8 @@ void finalize(Server *S, Request *R) {
   try {
     ReqCtx *ctx = S->reqtab.as<ReqCtx>() + R->slot;
     number_clusters(R->lmin.as<int32_t>(), R->n, R->d_out.as<int32_t>(), R->ws, S->astream);
-    WCC_CUDA(cudaMemcpyAsync(R->h_out, R->d_out.p, 4 * R->n, cudaMemcpyDeviceToHost, S->astream));
+    WCC_CUDA(cudaMemcpyAsync(R->h_out.data(), R->d_out.p, 4 * R->n, cudaMemcpyDeviceToHost,
+                             S->astream));
     ReqCtx h = read_back(ctx, S->astream);
     R->stats.in_clusters = R->gi.clusters;
     R->stats.out_clusters = h.accepted;
@@ -217,7 +218,7 @@ void admit(Server *S, Request *R) {
       R->h_src = R->h_dst = nullptr;
     }
     int32_t *d_in = static_cast<int32_t *>(R->d_in.ensure(4 * n));
-    WCC_CUDA(cudaMemcpyAsync(d_in, R->h_in, 4 * n, cudaMemcpyHostToDevice, s));
+    WCC_CUDA(cudaMemcpyAsync(d_in, R->h_in.data(), 4 * n, cudaMemcpyHostToDevice, s));
     auto t0 = clock_t_::now();
     R->gi = group_by_label(R->g->off.as<int64_t>(), n, d_in, R->min_size, R->ws, s);
     R->stats.ms_membership =
@@ -448,9 +449,8 @@ uint64_t submit(Server *S, Graph *g, const int32_t *src, const int32_t *dst, int
     fail(WCC_ERR_BUSY, "the graph is too large for the server's queue");
   R->t_submit = clock_t_::now();
   if (R->n > 0) {
-    WCC_CUDA(cudaHostAlloc((void **)&R->h_in, 4 * R->n, cudaHostAllocDefault));
-    WCC_CUDA(cudaHostAlloc((void **)&R->h_out, 4 * R->n, cudaHostAllocDefault));
-    std::memcpy(R->h_in, labels, 4 * R->n);
+    R->h_in.assign(labels, labels + R->n);
+    R->h_out.resize((size_t)R->n);
   }
   if (!g) {
     R->h_src = src;
@@ -484,7 +484,7 @@ int collect(Server *S, std::unique_lock<std::mutex> &lk, uint64_t ticket, int32_
   if (R->status != WCC_OK) fail(R->status, R->error);
   if (R->n > 0) {
     if (!out) fail(WCC_ERR_INVALID, "clustering_out is NULL");
-    std::memcpy(out, R->h_out, 4 * R->n);
+    std::memcpy(out, R->h_out.data(), 4 * R->n);
   }
   if (stats) *stats = R->stats;
   return WCC_OK;
