@@ -224,3 +224,31 @@ def test_serving_edge_request_refusals(wcc):
         out, _ = srv.wait(t, timeout_ms=60_000)
     with wcc.WccGraph.from_edges(w.src, w.dst, w.n) as g:
         assert np.array_equal(out, g.run(w.labels))
+
+
+def test_serving_submit_does_not_wait_for_the_device(wcc):
+    """A submission while the kernel is busy returns at once: nothing on the
+    submit path waits for the whole device (pinning host memory per request
+    did, and stalled every submission until the backlog had drained)."""
+    from synth import gpu_graphs
+    big = gpu_graphs.dcpp_1m(seed=0)
+    small = synth.lfr_like(5_000, seed=4)
+    with wcc.WccGraph.from_edges(big.src, big.dst, big.n) as gb, \
+            wcc.WccGraph.from_edges(small.src, small.dst, small.n) as gs:
+        _, st = gb.run(big.labels, min_size=big.min_size, stats=True)
+        busy_ms = st["ms_refine"]
+        ref_small = gs.run(small.labels)
+        lab_big = big.labels.cpu().numpy()
+        import time
+        with wcc.WccServer(16 << 30) as srv:
+            tb = srv.submit(gb, lab_big, min_size=big.min_size)
+            times, tickets = [], []
+            for _ in range(10):
+                t0 = time.perf_counter()
+                tickets.append(srv.submit(gs, small.labels))
+                times.append((time.perf_counter() - t0) * 1e3)
+            outs = [srv.wait(t, timeout_ms=120_000)[0] for t in tickets]
+            srv.wait(tb, timeout_ms=120_000)
+    assert max(times) < busy_ms / 2, (times, busy_ms)
+    for out in outs:
+        assert np.array_equal(out, ref_small)
