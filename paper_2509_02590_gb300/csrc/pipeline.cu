@@ -110,6 +110,45 @@ __global__ void k_size_keys(const int64_t *__restrict__ cstart, const uint32_t *
   vals[c] = (uint32_t)c;
 }
 
+// The same order for at most ORDER_SMALL clusters in one block: the keys of
+// k_size_keys paired with the cluster index (which breaks ties as the
+// stable sort does), sorted by a bitonic network in shared memory, and the
+// kept clusters' ranks written as k_invert does.
+constexpr int ORDER_SMALL = 4096;
+__global__ void __launch_bounds__(1024) k_order_small(const int64_t *__restrict__ cstart,
+                                                      const uint32_t *__restrict__ keep, int64_t K,
+                                                      uint32_t max_n, int64_t nkept,
+                                                      uint32_t *qidx) {
+  __shared__ unsigned long long a[ORDER_SMALL];
+  int P = 2;
+  while (P < K) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    unsigned long long v = ~0ull;
+    if (i < K) {
+      const uint32_t sz = (uint32_t)(cstart[i + 1] - cstart[i]);
+      const uint32_t key = keep[i] ? max_n - sz : max_n + 1;
+      v = ((unsigned long long)key << 32) | (unsigned)i;
+    }
+    a[i] = v;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long x = a[i], y = a[l];
+          if ((x > y) == ((i & k) == 0)) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < nkept; i += blockDim.x) qidx[(uint32_t)a[i]] = (uint32_t)i;
+}
+
 __global__ void k_invert(const uint32_t *__restrict__ order, int64_t nkept, uint32_t *qidx) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nkept) qidx[order[i]] = (uint32_t)i;
@@ -258,7 +297,12 @@ GroupInfo group_by_label(const int64_t *off, int64_t n, const int32_t *labels, i
   gi.max_n = (int64_t)hi.max_n;
   gi.max_dsum = (int64_t)hi.max_dsum;
   const int64_t K = gi.clusters;
-  if (gi.kept > 1) {
+  if (gi.kept > 1 && K <= ORDER_SMALL) {
+    // queue order: largest input clusters first (qidx = rank by size), in one block
+    k_order_small<<<1, 1024, 0, s>>>(cstart, keep, K, (uint32_t)gi.max_n, gi.kept, qidx);
+    note_launch();
+    WCC_CUDA(cudaGetLastError());
+  } else if (gi.kept > 1) {
     // queue order: largest input clusters first (qidx = rank by size)
     uint32_t *ok1 = buf<uint32_t>(ws, B_OK1, K);
     uint32_t *ov1 = buf<uint32_t>(ws, B_OV1, K);
