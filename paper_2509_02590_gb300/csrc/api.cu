@@ -543,20 +543,23 @@ void run_impl(Graph *g, const int32_t *lab_in, const wcc_threshold_rule *rule, i
     if (p.prof) dump_item_profile(p, prof_path, mode == WCC_MODE_BATCHED ? grid : 0, s);
   }
   tm.mark(2, s);
+  // ---- a9: ids = rank of each accepted cluster's smallest vertex, numbered
+  // into the staging buffer right behind the kernel; the run's counters are
+  // read after it (one wait for both), and the result reaches clustering_out
+  // only once they show no error
+  int32_t *d_out = static_cast<int32_t *>(rb[R_OUT].ensure(4 * n));
+  number_clusters(lmin, n, d_out, g->ws, s);
+  tm.mark(3, s);
   RunCounters hc{};
   ReqCtx hr{};
   if (gi.kept > 0) {
-    hc = read_back(ctr, s);
+    WCC_CUDA(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaMemcpyAsync(&hr, req, sizeof(hr), cudaMemcpyDeviceToHost, s));
+    WCC_CUDA(cudaStreamSynchronize(s));
     check_derr(hc.error, "refinement");
-    hr = read_back(req, s);
   }
-
-  // ---- a9: ids = rank of each accepted cluster's smallest vertex
-  int32_t *d_out = lab_out;
-  if (!on_device) d_out = static_cast<int32_t *>(rb[R_OUT].ensure(4 * n));
-  number_clusters(lmin, n, d_out, g->ws, s);
-  tm.mark(3, s);
-  if (!on_device) WCC_CUDA(cudaMemcpyAsync(lab_out, d_out, 4 * n, cudaMemcpyDeviceToHost, s));
+  WCC_CUDA(cudaMemcpyAsync(lab_out, d_out, 4 * n,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   WCC_CUDA(cudaStreamSynchronize(s));
 
   if (stats) {
