@@ -80,6 +80,87 @@ __device__ int block_scan_inplace(int32_t *a, int n, int32_t *tmp) {
   return carry;
 }
 
+// CPM local moving by one warp over a part's state at ws (the layout of
+// cda_words).  Instantiated once with ws derived from the block's shared
+// array and once for the global scratch, so that each loop addresses its
+// own space directly rather than through generic loads.
+__device__ __forceinline__ void cpm_local_moving(int32_t *ws, int n, long long gnum,
+                                                 long long gden) {
+  const int lane = threadIdx.x & 31;
+  int32_t *off = ws + n, *comm = off + n + 1, *size = comm + n, *kc = size + 2 * n;
+  const int32_t *adj = kc + 2 * n;
+  for (int sweep = 0; sweep < CPM_MAX_SWEEPS; ++sweep) {
+    int moved = 0;
+    for (int v = 0; v < n; ++v) {
+      const int c0 = comm[v], b = off[v], e = off[v + 1];
+      // the first 32 neighbours' communities stay in a register for the
+      // three passes below (most rows are that short)
+      const int cu0 = b + lane < e ? comm[adj[b + lane]] : -1;
+      // neighbours' communities counted, one shared atomic a neighbour
+      // (grouping equal communities by a warp match first took longer than
+      // the atomics' address conflicts it saves)
+      for (int q0 = b; q0 < e; q0 += 32) {
+        const int q = q0 + lane;
+        const int cu = q0 == b ? cu0 : (q < e ? comm[adj[q]] : -1);
+        if (cu >= 0) atomicAdd(&kc[cu], 1);
+      }
+      __syncwarp();
+      const long long s0 = size[c0] - 1;  // c0 without v
+      const long long g0 = (long long)kc[c0] * gden - gnum * s0;
+      long long bg = LLONG_MIN;
+      int bc = INT_MAX;
+      for (int q = b + lane; q < e; q += 32) {
+        const int cu = q < b + 32 ? cu0 : comm[adj[q]];
+        if (cu == c0) continue;
+        const long long g = (long long)kc[cu] * gden - gnum * (long long)size[cu];
+        if (g > bg || (g == bg && cu < bc)) {
+          bg = g;
+          bc = cu;
+        }
+      }
+      if (lane == 0 && s0 > 0) {  // the empty community n + v
+        const int ce = n + v;
+        if (0 > bg || (0 == bg && ce < bc)) {
+          bg = 0;
+          bc = ce;
+        }
+      }
+      // the warp's best: largest gain (its order-preserving unsigned image
+      // reduced high word, then low word), then the smallest id
+      {
+        const bool has = bc != INT_MAX;
+        const unsigned long long ug = (unsigned long long)bg ^ 0x8000000000000000ull;
+        const unsigned hi = has ? (unsigned)(ug >> 32) : 0u;
+        const unsigned mhi = __reduce_max_sync(FULL, hi);
+        const bool h1 = has && hi == mhi;
+        const unsigned mlo = __reduce_max_sync(FULL, h1 ? (unsigned)ug : 0u);
+        const bool h2 = h1 && (unsigned)ug == mlo;
+        const unsigned mid = __reduce_max_sync(FULL, h2 ? ~(unsigned)bc : 0u);
+        if (__ballot_sync(FULL, has)) {
+          bc = (int)~mid;
+          bg = (long long)((((unsigned long long)mhi << 32) | mlo) ^ 0x8000000000000000ull);
+        } else {
+          bc = INT_MAX;
+          bg = LLONG_MIN;
+        }
+      }
+      __syncwarp();
+      for (int q = b + lane; q < e; q += 32) kc[q < b + 32 ? cu0 : comm[adj[q]]] = 0;
+      __syncwarp();
+      if (bc != INT_MAX && bg > g0) {
+        if (lane == 0) {
+          comm[v] = bc;
+          size[c0] -= 1;
+          size[bc] += 1;
+        }
+        ++moved;
+      }
+      __syncwarp();
+    }
+    if (moved == 0) break;
+  }
+}
+
 __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, unsigned long long nparts,
                                             const ReqCtx *__restrict__ reqs, long long gnum,
                                             long long gden, int32_t *partof, int32_t *loc,
@@ -155,78 +236,13 @@ __global__ void __launch_bounds__(CB, 1) k_cda(const Item *__restrict__ parts, u
       kc[n + i] = 0;
     }
     __syncthreads();
-    // CPM local moving, one warp
+    // CPM local moving, one warp, on the state in shared memory or in the
+    // global scratch
     if (threadIdx.x < 32) {
-      for (int sweep = 0; sweep < CPM_MAX_SWEEPS; ++sweep) {
-        int moved = 0;
-        for (int v = 0; v < n; ++v) {
-          const int c0 = comm[v], b = off[v], e = off[v + 1];
-          // the first 32 neighbours' communities stay in a register for the
-          // three passes below (most rows are that short)
-          const int cu0 = b + lane < e ? comm[adj[b + lane]] : -1;
-          // neighbours' communities counted, one atomic per community a chunk
-          // (most neighbours share a few communities)
-          for (int q0 = b; q0 < e; q0 += 32) {
-            const int q = q0 + lane;
-            const int cu = q0 == b ? cu0 : (q < e ? comm[adj[q]] : -1);
-            const unsigned peers = __match_any_sync(FULL, cu);
-            if (cu >= 0 && (peers & lanemask_lt()) == 0) atomicAdd(&kc[cu], __popc(peers));
-          }
-          __syncwarp();
-          const long long s0 = size[c0] - 1;  // c0 without v
-          const long long g0 = (long long)kc[c0] * gden - gnum * s0;
-          long long bg = LLONG_MIN;
-          int bc = INT_MAX;
-          for (int q = b + lane; q < e; q += 32) {
-            const int cu = q < b + 32 ? cu0 : comm[adj[q]];
-            if (cu == c0) continue;
-            const long long g = (long long)kc[cu] * gden - gnum * (long long)size[cu];
-            if (g > bg || (g == bg && cu < bc)) {
-              bg = g;
-              bc = cu;
-            }
-          }
-          if (lane == 0 && s0 > 0) {  // the empty community n + v
-            const int ce = n + v;
-            if (0 > bg || (0 == bg && ce < bc)) {
-              bg = 0;
-              bc = ce;
-            }
-          }
-          // the warp's best: largest gain (its order-preserving unsigned image
-          // reduced high word, then low word), then the smallest id
-          {
-            const bool has = bc != INT_MAX;
-            const unsigned long long ug = (unsigned long long)bg ^ 0x8000000000000000ull;
-            const unsigned hi = has ? (unsigned)(ug >> 32) : 0u;
-            const unsigned mhi = __reduce_max_sync(FULL, hi);
-            const bool h1 = has && hi == mhi;
-            const unsigned mlo = __reduce_max_sync(FULL, h1 ? (unsigned)ug : 0u);
-            const bool h2 = h1 && (unsigned)ug == mlo;
-            const unsigned mid = __reduce_max_sync(FULL, h2 ? ~(unsigned)bc : 0u);
-            if (__ballot_sync(FULL, has)) {
-              bc = (int)~mid;
-              bg = (long long)((((unsigned long long)mhi << 32) | mlo) ^ 0x8000000000000000ull);
-            } else {
-              bc = INT_MAX;
-              bg = LLONG_MIN;
-            }
-          }
-          __syncwarp();
-          for (int q = b + lane; q < e; q += 32) kc[q < b + 32 ? cu0 : comm[adj[q]]] = 0;
-          __syncwarp();
-          if (bc != INT_MAX && bg > g0) {
-            if (lane == 0) {
-              comm[v] = bc;
-              size[c0] -= 1;
-              size[bc] += 1;
-            }
-            ++moved;
-          }
-          __syncwarp();
-        }
-        if (moved == 0) break;
-      }
+      if (ws == smem_ws)
+        cpm_local_moving(smem_ws, n, gnum, gden);
+      else
+        cpm_local_moving(ws, n, gnum, gden);
     }
     __syncthreads();
     // the connected parts of every community
