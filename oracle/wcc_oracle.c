@@ -496,8 +496,10 @@ static int cmp_vset_min(const void *a, const void *b) {
  *   g(c) = k(v, c) * gden - gnum * n_c,
  * k(v, c) = edges from v into c and n_c counted without v; joining an
  * empty community gains 0.  The candidates are the communities of v's
- * neighbours other than c0 and, when c0 holds more than v, the empty
- * community numbered n + v (community ids are 0..2n-1; v starts in v).  The
+ * neighbours other than c0 and, when c0 holds more than v, an empty
+ * community: the id n + v when nobody holds it, else the smallest id nobody
+ * holds (community ids are 0..2n-1, at most n of them held; v starts in v;
+ * n + v is held when v moved there and others joined it).  The
  * best candidate has the largest gain, ties to the smallest community id; v
  * moves there only when that gain is strictly above g(c0), so every move
  * raises Q and the sweeps end.  Finally (connected != 0, as CM uses it)
@@ -538,8 +540,11 @@ static int32_t cpm_communities(const lgraph *H, int64_t gnum, int64_t gden, int3
           bestg = g;
         }
       }
-      if (size[c0] > 0) { /* the empty community n + v */
-        const int32_t ce = n + v;
+      if (size[c0] > 0) { /* an empty community: n + v, else the smallest empty id */
+        int32_t ce = n + v;
+        if (size[ce] != 0)
+          for (ce = 0; size[ce] != 0; ce++) {
+          }
         if (best < 0 || 0 > bestg || (0 == bestg && ce < best)) {
           best = ce;
           bestg = 0;

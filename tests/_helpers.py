@@ -155,3 +155,33 @@ def contract_passes(n, eu, ev, k):
             break
         rep = svs[sets_of(len(svs), qu, qv, mask)[idx]]
     return rep, passes
+
+
+# A 17-vertex graph, found by a seeded search over random graphs, on which
+# CPM local moving at resolution 2/5 brings a vertex v to share the id n + v
+# with vertices that joined it there while v's best move is to be alone
+# (the corner case of the empty-community candidate).
+TAKEN_ID_CASE = dict(
+    n=17, gnum=2, gden=5,
+    eu=[0, 0, 0, 0, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 4, 4, 4, 4, 5, 5, 5, 6, 6, 6, 6, 7, 8, 8, 8,
+        8, 9, 10, 10, 10, 11, 12, 12, 14],
+    ev=[8, 9, 14, 15, 14, 3, 7, 8, 9, 14, 5, 9, 12, 14, 16, 7, 8, 11, 12, 10, 13, 14, 9, 10, 14,
+        16, 10, 9, 11, 12, 13, 14, 11, 14, 16, 14, 14, 16, 15])
+
+
+def taken_id_cm_input(clique: int = 5):
+    """One input cluster: TAKEN_ID_CASE's graph joined to a clique on the
+    next `clique` ids by the single edge 1-17, so that the cut split hands
+    the 17-vertex graph to the community step whole.  Returns
+    (n, src, dst, labels, min_size, gnum, gden)."""
+    c = TAKEN_ID_CASE
+    n = c["n"] + clique
+    eu, ev = list(c["eu"]), list(c["ev"])
+    for i in range(c["n"], n):
+        for j in range(i + 1, n):
+            eu.append(i)
+            ev.append(j)
+    eu.append(1)
+    ev.append(c["n"])
+    return (n, np.array(eu, np.int32), np.array(ev, np.int32), np.zeros(n, np.int32), 2,
+            c["gnum"], c["gden"])

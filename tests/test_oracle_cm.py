@@ -24,6 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests._helpers import TAKEN_ID_CASE
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLDEN = json.load(open(os.path.join(HERE, "golden", "hand_traced.json")))
@@ -228,3 +229,16 @@ def _edge_list(sub):
                 eu.append(v)
                 ev.append(u)
     return np.array(eu, np.int32), np.array(ev, np.int32)
+
+
+
+def test_cpm_local_optimum_where_the_id_n_plus_v_is_taken():
+    """The 17-vertex graph of tests/_helpers.py: a vertex comes to share the
+    id n + v with vertices that joined it there while its best move is to be
+    alone; the empty community offered must then be another, empty id, or
+    the vertex stays where it gains less than alone and the sweeps never
+    settle (the local optimum fails)."""
+    c = TAKEN_ID_CASE
+    eu, ev = np.array(c["eu"], np.int32), np.array(c["ev"], np.int32)
+    comm = oracle.cpm_communities(c["n"], eu, ev, c["gnum"], c["gden"], connected=False)
+    assert _gains_ok(c["n"], _adj(c["n"], eu, ev), comm.tolist(), c["gnum"], c["gden"])
