@@ -21,8 +21,9 @@
 // of its community c0, would gain g(c) = k(v, c) * gden - gnum * n_c by
 // joining community c (k = edges from v into c, n_c its size without v); an
 // empty community gains 0.  Candidates: the communities of v's neighbours
-// other than c0, and, when c0 holds more than v, the empty community n + v
-// (community ids run over 0..2n-1, v starting in v).  The largest gain wins,
+// other than c0, and, when c0 holds more than v, an empty community: n + v
+// when nobody holds it, else the smallest id nobody holds (community ids run
+// over 0..2n-1, v starting in v).  The largest gain wins,
 // ties to the smallest id, and v moves only when it beats g(c0).
 #include <algorithm>
 #include <climits>
@@ -118,8 +119,19 @@ __device__ __forceinline__ void cpm_local_moving(int32_t *ws, int n, long long g
           bc = cu;
         }
       }
-      if (lane == 0 && s0 > 0) {  // the empty community n + v
-        const int ce = n + v;
+      // an empty community: n + v when nobody holds it, else the smallest id
+      // nobody holds (size[c0] still counts v here, so c0 never looks empty;
+      // at most n of the 2n ids are held)
+      int ce = n + v;
+      if (s0 > 0 && size[ce] != 0) {
+        ce = -1;
+        for (int b0 = 0; ce < 0 && b0 < 2 * n; b0 += 32) {
+          const int i = b0 + lane;
+          const unsigned z = __ballot_sync(FULL, i < 2 * n && size[i] == 0);
+          if (z) ce = b0 + __ffs(z) - 1;
+        }
+      }
+      if (lane == 0 && s0 > 0 && ce >= 0) {
         if (0 > bg || (0 == bg && ce < bc)) {
           bg = 0;
           bc = ce;

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import synth
+from tests._helpers import taken_id_cm_input
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -115,3 +116,14 @@ def test_cm_device_buffers_and_resolution_checks(wcc):
             with pytest.raises(wcc.WccError) as ei:
                 g.run_cm(w.labels, bad)
             assert ei.value.status == -1
+
+
+def test_cm_empty_community_when_n_plus_v_is_taken(wcc):
+    """A part on which a vertex's best move is to be alone while the id n + v
+    is held by vertices that joined it there: the kernel offers the smallest
+    empty id instead, as the oracle does (the result differs from offering
+    n + v itself)."""
+    n, src, dst, labels, min_size, gnum, gden = taken_id_cm_input()
+    ref, rst, got, st = _both(wcc, n, src, dst, labels, min_size, gnum, gden)
+    assert rst["splits"] >= 1
+    assert np.array_equal(got, ref)
