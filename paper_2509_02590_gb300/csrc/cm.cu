@@ -93,7 +93,9 @@ __device__ __forceinline__ void cpm_local_moving(int32_t *ws, int n, long long g
   for (int sweep = 0; sweep < CPM_MAX_SWEEPS; ++sweep) {
     int moved = 0;
     for (int v = 0; v < n; ++v) {
-      const int c0 = comm[v], b = off[v], e = off[v + 1];
+      // n + v's size is read with the row (sizes change only at a move,
+      // after the step's last use of it)
+      const int c0 = comm[v], b = off[v], e = off[v + 1], szn = size[n + v];
       // the first 32 neighbours' communities stay in a register for the
       // three passes below (most rows are that short)
       const int cu0 = b + lane < e ? comm[adj[b + lane]] : -1;
@@ -123,7 +125,7 @@ __device__ __forceinline__ void cpm_local_moving(int32_t *ws, int n, long long g
       // nobody holds (size[c0] still counts v here, so c0 never looks empty;
       // at most n of the 2n ids are held)
       int ce = n + v;
-      if (s0 > 0 && size[ce] != 0) {
+      if (s0 > 0 && szn != 0) {
         ce = -1;
         for (int b0 = 0; ce < 0 && b0 < 2 * n; b0 += 32) {
           const int i = b0 + lane;
