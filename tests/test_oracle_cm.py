@@ -296,3 +296,26 @@ def test_cpm_sweeps_match_a_restatement():
     for n, eu, ev, gnum, gden in cases:
         got = oracle.cpm_communities(n, eu, ev, gnum, gden, connected=False).tolist()
         assert got == _restated_local_moving(n, _adj(n, eu, ev), gnum, gden), (n, gnum, gden)
+
+
+def test_cm_idempotent():
+    """CM output clusters are well connected (lambda > T after no peel), so
+    CM run again on its own output accepts each of them whole: no cut
+    split, so no community step, and the same clusters come back."""
+    rng = np.random.default_rng(6)
+    for t in range(20):
+        k = int(rng.integers(2, 6))
+        sizes = rng.integers(6, 30, size=k)
+        n = int(sizes.sum())
+        blk = np.repeat(np.arange(k), sizes)
+        iu, ju = np.triu_indices(n, 1)
+        pr = np.where(blk[iu] == blk[ju], float(rng.uniform(0.3, 0.8)), float(rng.uniform(0.0, 0.05)))
+        keep = rng.random(len(iu)) < pr
+        eu, ev = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+        labels = (blk // 2).astype(np.int32)
+        gnum, gden = int(rng.integers(1, 4)), int(rng.choice([10, 100]))
+        off, adj = oracle.build_csr(n, eu, ev)
+        out, _ = oracle.cm(n, off, adj, labels, 2, gnum, gden)
+        again, st = oracle.cm(n, off, adj, out, 2, gnum, gden)
+        assert again.tolist() == out.tolist()
+        assert st["splits"] == 0
