@@ -153,9 +153,12 @@ int wcc_run(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshol
  * sweeps over the part's vertices in ascending id, from singletons, at most
  * 64 sweeps or until one moves nothing; a vertex taken out of its community
  * c0 joins the neighbouring community c of largest gain
- * k(v,c) * cpm_den - cpm_num * |c| (or an empty community, gain 0), ties to
- * the smallest community id, and only when that gain beats staying in c0;
- * then every community is split into its connected parts.  Arguments,
+ * k(v,c) * cpm_den - cpm_num * |c| (|c| without v; or, when c0 keeps other
+ * members, an empty community with gain 0: the id n + v while no vertex holds
+ * it, else the smallest id no vertex holds, with community ids 0..2n-1 over
+ * the part's n vertices and vertex v starting in v), ties to the smallest
+ * community id, and only when that gain beats staying in c0; then every
+ * community is split into its connected parts.  Arguments,
  * layouts and results as wcc_run.  WCC_ERR_INVALID unless
  * 0 <= cpm_num <= 2^31 and 1 <= cpm_den <= 2^31. */
 int wcc_run_cm(const wcc_graph *g, const int32_t *clustering_in, const wcc_threshold_rule *rule,
