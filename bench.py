@@ -543,6 +543,25 @@ def cm_record(wcc, torch, w, src_d, dst_d, lab_d, flush, runs=5):
     return rec
 
 
+def latency_by_size(edges, lat_ms, cuts=(10 ** 5, 10 ** 6)):
+    """p50/p99 latency (ms) of the requests in each edge-count band: below
+    cuts[0], [cuts[0], cuts[1]), and from cuts[1] up.  edges and lat_ms are
+    per request, in the same order; empty bands are left out."""
+    def short(x):
+        return f"{x // 10 ** 6}M" if x % 10 ** 6 == 0 else f"{x // 1000}k" if x % 1000 == 0 else str(x)
+
+    bands = ((0, cuts[0], f"<{short(cuts[0])}"),
+             (cuts[0], cuts[1], f"{short(cuts[0])}-{short(cuts[1])}"),
+             (cuts[1], None, f">={short(cuts[1])}"))
+    out = {}
+    for lo, hi, name in bands:
+        sel = sorted(l for e, l in zip(edges, lat_ms) if e >= lo and (hi is None or e < hi))
+        if sel:
+            q = lambda f: sel[min(len(sel) - 1, int(round(f * (len(sel) - 1))))]
+            out[name + " edges"] = {"requests": len(sel), "p50_ms": q(0.5), "p99_ms": q(0.99)}
+    return out
+
+
 # ------------------------------------------------------------------ ranks
 def aggregate_ranks(dist, torch, dev, total_ms: float, m: int, clusters: int):
     """Weak scaling across ranks: every rank refines its own instance with no
@@ -597,21 +616,23 @@ def serving_bench(wcc, np, torch, n_requests: int = 10_000, pool_size: int = 200
         server counters)."""
         gaps = rng.exponential(1.0 / rate, count) if rate else np.zeros(count)
         with wcc.WccServer(bud) as srv:
-            tickets = []
+            tickets, req_edges = [], []
             t0 = _t.perf_counter()
             nxt = t0
             for k, gap in zip(picks[:count], gaps):
                 nxt += gap
                 while _t.perf_counter() < nxt:
                     pass
-                s, d, n, lab, _ = pool[k]
+                s, d, n, lab, m = pool[k]
                 tickets.append(srv.submit_edges(s, d, n, lab))
+                req_edges.append(m)
             lat = []
             for t in tickets:
                 _, st = srv.wait(t)
                 lat.append(st["ms_total"])
             took = _t.perf_counter() - t0
-            info = srv.info()
+            info = dict(srv.info())
+        info["by_size"] = latency_by_size(req_edges, lat)
         return took, sorted(lat), info
 
     def p(lat, q):
@@ -625,6 +646,7 @@ def serving_bench(wcc, np, torch, n_requests: int = 10_000, pool_size: int = 200
         loads[str(load)] = {"offered_requests_per_s": load * cap_rps,
                             "requests_per_s": n_requests / run_s, "edges_per_s": edges / run_s,
                             "p50_ms": p(lat, 0.5), "p99_ms": p(lat, 0.99),
+                            "by_size": info["by_size"],
                             "peak_active": info["peak_active"],
                             "peak_used_bytes": info["peak_used_bytes"]}
     tight_edges = sum(pool[k][4] for k in picks[:tight_requests])
